@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Throughput of the fused RLB time step on GB300.
+
+Workload: the 3-D shock-cloud, 512 x 256 x 256 cells (33.5 M), FP32
+population storage with FP64 moments and recovery; a step is one time step
+of the whole grid (every cell: minmod streaming of 38 populations, bulk
+Laplacian, moments, Landau recovery, equilibria, implicit update).  The FP64
+form is timed on the same grid for the FP32/FP64 ratio, and the FP32 form's
+L1 error against the FP64 form is measured on the 800-cell tube.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun as independent replicas (the step has no exchange
+between ranks in this configuration); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS and % of HBM peak; FP32-storage vs FP64 form at stated L1 error"
+UNIT = "MLUPS"
+# algorithmic bytes per cell update: 38 populations read and written once,
+# 5 previous-level macroscopic values read and written once
+BYTES_FP32 = 38 * 4 * 2 + 5 * 4 * 2     # 344
+BYTES_FP64 = 38 * 8 * 2 + 5 * 8 * 2     # 688
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region"""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.lines:
+            return None
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rejected(clk):
+    if clk is None:
+        return False
+    if set(clk["reasons"]) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    return clk["sm_max_mhz"] and clk["sm_mhz"] < 0.6 * clk["sm_max_mhz"] and not clk["reasons"]
+
+
+def timed_steps(torch, g, steps, warmup, device_index):
+    """warm up, then time `steps` steps with CUDA events on the launching stream"""
+    g.step(warmup)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    for attempt in range(2):
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(device_index) as cs:
+            barrier()
+            torch.cuda.synchronize()
+            l0 = g.launches
+            start.record(stream)
+            g.step(steps)
+            end.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+        ms = start.elapsed_time(end)
+        launches = g.launches - l0
+        clk = cs.summary()
+        if not rejected(clk):
+            break
+    return ms, clk, launches
+
+
+_dist = None
+
+
+def barrier():
+    if _dist is not None:
+        _dist.barrier()
+
+
+def max_over_ranks(torch, v: float) -> float:
+    if _dist is None:
+        return v
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    _dist.all_reduce(t, op=_dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(steps=None, warmup=1, budget_s=12.0):
+    """the oracle, as it stands, on a bounded sample of the workload: the same
+    shock-cloud shrunk 8x per axis (64 x 32 x 32 cells), FP64, all host cores"""
+    import oracle
+    from paper_1302_1125_gb300 import workloads as W
+    oracle.set_threads(os.cpu_count() or 1)
+    w = W.cloud_3d(scale=8, precision=W.FP64)
+    p = oracle.Params(nx=w.nx, ny=w.ny, nz=w.nz, bc_lo=w.bc_lo, bc_hi=w.bc_hi, dt=w.dt_over_dx,
+                      eta_over_s=w.eta_over_s, zeta_over_s=w.zeta_over_s,
+                      alpha_override=w.alpha_override, inlet_n=w.inlet[0], inlet_T=w.inlet[1],
+                      inlet_u=tuple(w.inlet[2]))
+    s = oracle.init(p, *w.fields())
+    oracle.step(s, warmup)
+    if steps is None:
+        t0 = time.perf_counter()
+        oracle.step(s, 2)
+        per = (time.perf_counter() - t0) / 2
+        steps = max(2, int(budget_s / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    oracle.step(s, steps)
+    el = time.perf_counter() - t0
+    return {"value": w.N * steps / el / 1e6, "unit": UNIT, "cores": oracle.get_threads(),
+            "kind": "oracle",
+            "sample": f"{w.name}: {w.nx}x{w.ny}x{w.nz} cells (the 512x256x256 shock-cloud shrunk 8x "
+                      f"per axis), {steps} FP64 steps, {el:.1f} s"}, steps, el
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    base, steps, el = cpu_baseline(steps=args.steps, warmup=args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": base["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cloud_3d 512x256x256 shock-cloud (oracle on the 64x32x32 "
+                                   "sample of the same workload)"},
+            "cpu_baseline": base,
+            "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def l1_fp32_vs_fp64(torch):
+    from paper_1302_1125_gb300 import rlb
+    from paper_1302_1125_gb300 import workloads as W
+    w = W.tube_800()
+    out = []
+    for prec in (rlb.FP32_STORAGE, rlb.FP64):
+        g = rlb.Grid.from_workload(w, precision=prec)
+        g.init(*w.fields()).step(w.steps)
+        out.append(g.macroscopic(device=False))
+        g.close()
+    a, b = out
+    return {"workload": f"tube_800, {w.steps} steps",
+            "n": float(np.abs(a[0] - b[0]).sum() / np.abs(b[0]).sum()),
+            "e": float(np.abs(a[1] - b[1]).sum() / np.abs(b[1]).sum()),
+            "u_x": float(np.abs(a[2] - b[2]).sum() / np.abs(b[2]).sum())}
+
+
+def run_ours(args):
+    global _dist
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        _dist = dist
+    else:
+        torch.cuda.set_device(0)
+    from paper_1302_1125_gb300 import build as B
+    B.build()
+    from paper_1302_1125_gb300 import rlb
+    from paper_1302_1125_gb300 import workloads as W
+
+    hbm_peak, peak_kind = peaks()
+    w = W.cloud_3d()
+    N = w.N
+    fields = w.fields()
+    dev_fields = [torch.as_tensor(a, device="cuda") for a in fields]
+
+    # FP32-storage form (the headline)
+    g = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE)
+    g.init(*dev_fields)
+    ms, clk, launches = timed_steps(torch, g, args.steps, args.warmup, local)
+    ms = max_over_ranks(torch, ms)
+    per_step = ms / args.steps
+    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    achieved = BYTES_FP32 * N / (per_step * 1e-3) / 1e9
+    g.close()
+
+    # FP64 form on the same grid
+    g64 = rlb.Grid.from_workload(w, precision=rlb.FP64)
+    g64.init(*dev_fields)
+    k64 = max(3, args.steps // 10)
+    ms64, _, _ = timed_steps(torch, g64, k64, max(3, args.warmup), local)
+    ms64 = max_over_ranks(torch, ms64)
+    value64 = world * N * k64 / (ms64 * 1e-3) / 1e6
+    ach64 = BYTES_FP64 * N / (ms64 / k64 * 1e-3) / 1e9
+    g64.close()
+    del dev_fields
+
+    # end to end through the public API with host buffers: pinned host fields
+    # -> rlb_init -> K steps -> rlb_macroscopic into pinned host memory
+    host_in = [torch.from_numpy(a).pin_memory() for a in fields]
+    host_out = torch.empty((6, N), dtype=torch.float64).pin_memory()
+    ge = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE)
+    ge.init(*[a.numpy() for a in host_in]).step(args.warmup)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    ge.init(*[a.numpy() for a in host_in])
+    ge.step(args.steps)
+    rlb.rlb_macroscopic(ge.ctx, host_out.numpy(), 0)
+    torch.cuda.synchronize()
+    e2e_s = max_over_ranks(torch, time.perf_counter() - t0)
+    barrier()
+    ge.close()
+    e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": 5 * 8 * N / args.steps, "d2h_bytes_per_step": 6 * 8 * N / args.steps,
+           "what": "pinned host n,T,u -> rlb_init -> K steps -> rlb_macroscopic to pinned host"}
+
+    if rank != 0:
+        return 0
+    l1 = l1_fp32_vs_fp64(torch)
+    base = cpu_baseline()[0] if world == 1 or rank == 0 else None
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 storage (f64 moments/recovery)",
+        "data": "synthetic",
+        "config": {"workload": "cloud_3d: 3-D shock-cloud 512x256x256 (slab-driven shock, pressure "
+                               "ratio 10; cloud r=48 at (180,128,128), density x10, pressure balanced); "
+                               "eta/s 0.05, alpha 0.2, dt/dx 0.15",
+                   "cells": N, "precision": "FP32 populations, FP64 moments and recovery",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                   "l2": "inputs larger than L2: 10.2 GB of populations read+written per step"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": None,
+                     "note": f"{BYTES_FP32} algorithmic bytes per cell update x {N} cells per launch "
+                             f"/ CUDA-event time per launch; peak {peak_kind} copy bandwidth"},
+        "fp64_form": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
+                      "hbm_achieved_gbs": ach64, "hbm_frac": ach64 / hbm_peak},
+        "fp32_over_fp64": value / value64,
+        "l1_error_fp32_vs_fp64": l1,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": base,
+    }
+    print(json.dumps(line), flush=True)
+    if _dist is not None:
+        _dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,451 @@
+// rlb_api.cu -- the C ABI of librlb (declared in include/rlb.h): argument
+// validation, device memory of a context, and the host side of every call.
+#include <cuda_runtime.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+
+#include "../../include/rlb.h"
+#include "rlb_device.cuh"
+#include "rlb_internal.h"
+
+using rlb::StepParams;
+
+struct rlb_ctx {
+    rlb_grid grid;
+    double eta_over_s, zeta_over_s, alpha;
+    int limiter;
+    rlb_options opt;
+    int device;
+    int N;
+    long long ps;      // plane stride (elements)
+    int dim;           // 1, 2 or 3: number of leading axes that are streamed
+    int fp32;
+    size_t esize;
+    void *block;       // the single device allocation
+    void *fbuf[2], *hbuf[2], *prev;
+    unsigned *d_status;
+    double *d_partial, *d_tot;
+    unsigned *h_status;   // pinned
+    double *h_tot;        // pinned
+    int cur;
+    cudaStream_t stream;
+    long long launches;
+    StepParams sp;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_err = "no error";
+
+rlb_status fail(rlb_ctx *ctx, rlb_status st, const std::string &msg)
+{
+    if (ctx)
+        ctx->err = msg;
+    else
+        g_err = msg;
+    return st;
+}
+
+rlb_status cuda_fail(rlb_ctx *ctx, cudaError_t e, const char *where)
+{
+    return fail(ctx, RLB_E_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define RLB_CUDA(ctx, call)                                        \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call); \
+    } while (0)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// alpha of Eq. 55 from zeta/s through Eq. 56 at the reference state
+// T = 1, lambda = 1 (s = 4n, P = n): alpha = 27 (zeta/s) s / (4 P nu^6)
+double alpha_from(double zeta_over_s, const rlb_options &o)
+{
+    if (o.alpha_override >= 0.0) return o.alpha_override;
+    return 27.0 * zeta_over_s * 4.0 / (4.0 * 2197.0);   // nu^6 = 13^3
+}
+
+int active_axes(const rlb_grid &g)
+{
+    return (g.nx > 1) + (g.ny > 1) + (g.nz > 1);
+}
+
+rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
+                    int limiter, const rlb_options &o, rlb_ctx *ctx)
+{
+    if (!grid) return fail(ctx, RLB_E_INVALID, "grid is NULL");
+    if (Q != RLB_Q) return fail(ctx, RLB_E_INVALID, "Q must be 19 (the extended D3Q19 lattice)");
+    const rlb_grid &g = *grid;
+    if (g.nx < 1 || g.ny < 1 || g.nz < 1) return fail(ctx, RLB_E_INVALID, "grid dimensions must be >= 1");
+    if ((long long)g.nx * g.ny * g.nz > (long long)INT_MAX)
+        return fail(ctx, RLB_E_INVALID, "grid has more than 2^31 - 1 cells");
+    bool inlet = false;
+    for (int a = 0; a < 3; ++a) {
+        for (int b : {g.bc_lo[a], g.bc_hi[a]}) {
+            if (b != RLB_BC_PERIODIC && b != RLB_BC_OUTFLOW && b != RLB_BC_INLET)
+                return fail(ctx, RLB_E_INVALID, "unknown boundary type");
+            if (b == RLB_BC_INLET) {
+                if (a != 0) return fail(ctx, RLB_E_INVALID, "inlet boundaries are supported on x faces only");
+                inlet = true;
+            }
+        }
+    }
+    if (inlet) {
+        const double u2 = g.inlet_u[0] * g.inlet_u[0] + g.inlet_u[1] * g.inlet_u[1] +
+                          g.inlet_u[2] * g.inlet_u[2];
+        if (!(g.inlet_n > 0.0) || !(g.inlet_T > 0.0) || !(u2 < 1.0) || !std::isfinite(g.inlet_n * g.inlet_T))
+            return fail(ctx, RLB_E_INVALID, "inlet state must have n > 0, T > 0, |u| < 1");
+    }
+    if (!(eta_over_s >= 0.0) || !std::isfinite(eta_over_s))
+        return fail(ctx, RLB_E_INVALID, "eta_over_s must be finite and >= 0");
+    if (!(zeta_over_s >= 0.0) || !std::isfinite(zeta_over_s))
+        return fail(ctx, RLB_E_INVALID, "zeta_over_s must be finite and >= 0");
+    if (limiter != RLB_LIMITER_MINMOD && limiter != RLB_LIMITER_NONE)
+        return fail(ctx, RLB_E_INVALID, "unknown limiter");
+    if (!(o.dt_over_dx > 0.0) || !std::isfinite(o.dt_over_dx))
+        return fail(ctx, RLB_E_INVALID, "dt_over_dx must be finite and > 0");
+    if (o.precision != RLB_FP64 && o.precision != RLB_FP32_STORAGE)
+        return fail(ctx, RLB_E_INVALID, "unknown precision");
+    if (o.euler_mode != 0 && o.euler_mode != 1) return fail(ctx, RLB_E_INVALID, "euler_mode must be 0 or 1");
+    if (!std::isfinite(o.tau_override) || !std::isfinite(o.alpha_override))
+        return fail(ctx, RLB_E_INVALID, "overrides must be finite");
+    // explicit stability bounds
+    const int d = active_axes(g) > 0 ? active_axes(g) : 1;
+    const double cmax = (d >= 2 ? 4.0 : 2.0) * rlb::kC0Ct;   // largest sum of |c_ia| c0/ct
+    if (o.dt_over_dx * cmax > 1.0)
+        return fail(ctx, RLB_E_UNSTABLE, "dt/dx exceeds the Courant bound of the extended lattice");
+    const double kb = rlb::kOmegaC * o.dt_over_dx * alpha_from(zeta_over_s, o);
+    if (2.0 * d * kb > 1.0)
+        return fail(ctx, RLB_E_UNSTABLE, "alpha dt exceeds the explicit diffusion bound");
+    return RLB_OK;
+}
+
+// inlet ghost values: f^eq and h^eq of the inlet state
+void inlet_ghosts(const rlb_grid &g, StepParams &sp)
+{
+    const double u2 = g.inlet_u[0] * g.inlet_u[0] + g.inlet_u[1] * g.inlet_u[1] +
+                      g.inlet_u[2] * g.inlet_u[2];
+    const double gam = 1.0 / std::sqrt(1.0 - (u2 < 1.0 ? u2 : 0.0));
+    rlb::Macro m;
+    m.P = g.inlet_n * g.inlet_T;
+    m.ux = gam * g.inlet_u[0];
+    m.uy = gam * g.inlet_u[1];
+    m.uz = gam * g.inlet_u[2];
+    m.n = g.inlet_n;
+    rlb::Coef<double> kf, kh;
+    rlb::coef_f(m, kf);
+    rlb::coef_h(m, kh);
+    double *gf = sp.ghost_f, *gh = sp.ghost_h;
+    [&]<int... I>(std::integer_sequence<int, I...>) {
+        ((gf[I] = rlb::eq_pop<I, true>(kf)), ...);
+        ((gh[I] = rlb::eq_pop<I, false>(kh)), ...);
+    }(std::make_integer_sequence<int, 19>{});
+}
+
+rlb_status check_device_status(rlb_ctx *ctx, rlb_status if_bad)
+{
+    RLB_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (*ctx->h_status != 0u) {
+        RLB_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
+        RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        return fail(ctx, if_bad, "a cell was non-physical (E <= |M|, n <= 0, |u| >= 1 or non-finite)");
+    }
+    return RLB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void rlb_default_options(rlb_options *o)
+{
+    if (!o) return;
+    o->dt_over_dx = 0.25;
+    o->tau_override = 0.0;
+    o->alpha_override = -1.0;
+    o->euler_mode = 0;
+    o->precision = RLB_FP64;
+    o->cuda_stream = nullptr;
+}
+
+rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
+                            int limiter, const rlb_options *opts)
+{
+    rlb_options o;
+    rlb_default_options(&o);
+    if (opts) o = *opts;
+    return validate(grid, Q, eta_over_s, zeta_over_s, limiter, o, nullptr);
+}
+
+rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
+                      int limiter, const rlb_options *opts, rlb_ctx **out)
+{
+    if (!out) return fail(nullptr, RLB_E_INVALID, "out is NULL");
+    *out = nullptr;
+    rlb_options o;
+    rlb_default_options(&o);
+    if (opts) o = *opts;
+    rlb_status st = validate(grid, Q, eta_over_s, zeta_over_s, limiter, o, nullptr);
+    if (st != RLB_OK) return st;
+
+    rlb_ctx *ctx = new (std::nothrow) rlb_ctx();
+    if (!ctx) return fail(nullptr, RLB_E_NOMEM, "host allocation failed");
+    ctx->grid = *grid;
+    ctx->eta_over_s = eta_over_s;
+    ctx->zeta_over_s = zeta_over_s;
+    ctx->limiter = limiter;
+    ctx->opt = o;
+    ctx->alpha = alpha_from(zeta_over_s, o);
+    ctx->N = grid->nx * grid->ny * grid->nz;
+    ctx->ps = (long long)align_up((size_t)ctx->N, 64);
+    ctx->dim = grid->nz > 1 ? 3 : (grid->ny > 1 ? 2 : 1);
+    ctx->fp32 = o.precision == RLB_FP32_STORAGE;
+    ctx->esize = ctx->fp32 ? 4 : 8;
+    ctx->stream = (cudaStream_t)o.cuda_stream;
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_fail(nullptr, e, "cudaGetDevice");
+    }
+
+    const size_t plane = (size_t)ctx->ps * ctx->esize;
+    const int nb = rlb::totals_blocks(ctx->N);
+    size_t off = 0;
+    size_t offs[8];
+    offs[0] = off; off += align_up(19 * plane, 256);   // f0
+    offs[1] = off; off += align_up(19 * plane, 256);   // h0
+    offs[2] = off; off += align_up(19 * plane, 256);   // f1
+    offs[3] = off; off += align_up(19 * plane, 256);   // h1
+    offs[4] = off; off += align_up(5 * plane, 256);    // prev
+    offs[5] = off; off += 256;                          // status
+    offs[6] = off; off += align_up(5 * sizeof(double) * nb, 256);   // partial sums
+    offs[7] = off; off += 256;                          // totals
+    e = cudaMalloc(&ctx->block, off);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return fail(nullptr, RLB_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    char *b = (char *)ctx->block;
+    ctx->fbuf[0] = b + offs[0];
+    ctx->hbuf[0] = b + offs[1];
+    ctx->fbuf[1] = b + offs[2];
+    ctx->hbuf[1] = b + offs[3];
+    ctx->prev = b + offs[4];
+    ctx->d_status = (unsigned *)(b + offs[5]);
+    ctx->d_partial = (double *)(b + offs[6]);
+    ctx->d_tot = (double *)(b + offs[7]);
+    e = cudaMallocHost(&ctx->h_status, sizeof(unsigned) + 8 * sizeof(double));
+    if (e != cudaSuccess) {
+        cudaFree(ctx->block);
+        delete ctx;
+        return fail(nullptr, RLB_E_NOMEM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+    }
+    ctx->h_tot = (double *)((char *)ctx->h_status + 8);
+    e = cudaMemsetAsync(ctx->block, 0, off, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        rlb_destroy(ctx);
+        return cuda_fail(nullptr, e, "cudaMemset");
+    }
+
+    StepParams &sp = ctx->sp;
+    std::memset(&sp, 0, sizeof(sp));
+    sp.nx = grid->nx;
+    sp.ny = grid->ny;
+    sp.nz = grid->nz;
+    sp.ps = ctx->ps;
+    for (int a = 0; a < 3; ++a) {
+        sp.bc_lo[a] = grid->bc_lo[a];
+        sp.bc_hi[a] = grid->bc_hi[a];
+    }
+    sp.half_lim = limiter == RLB_LIMITER_MINMOD ? 0.5 : 0.0;
+    sp.k1 = rlb::kC0Ct * o.dt_over_dx;
+    sp.k2 = 2.0 * rlb::kC0Ct * o.dt_over_dx;
+    sp.kw = rlb::kOmegaC * o.dt_over_dx;
+    sp.kbulk = rlb::kOmegaC * o.dt_over_dx * ctx->alpha;
+    sp.eta_over_s = eta_over_s;
+    sp.tau_override = o.tau_override;
+    sp.status = ctx->d_status;
+    inlet_ghosts(*grid, sp);
+    ctx->cur = 0;
+    ctx->err = "no error";
+    *out = ctx;
+    return RLB_OK;
+}
+
+rlb_status rlb_init(rlb_ctx *ctx, const double *n, const double *T, const double *ux,
+                    const double *uy, const double *uz, int on_device)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    if (!n || !T || !ux || !uy || !uz) return fail(ctx, RLB_E_INVALID, "a field pointer is NULL");
+    RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t bytes = sizeof(double) * (size_t)ctx->N;
+    const double *src[5] = {n, T, ux, uy, uz};
+    const double *dev[5];
+    if (on_device) {
+        for (int k = 0; k < 5; ++k) dev[k] = src[k];
+    } else {
+        // stage through the idle population buffer (38 ps esize >= 40 N bytes)
+        double *stage = (double *)ctx->fbuf[1 - ctx->cur];
+        for (int k = 0; k < 5; ++k) {
+            RLB_CUDA(ctx, cudaMemcpyAsync(stage + (size_t)k * ctx->N, src[k], bytes, cudaMemcpyHostToDevice,
+                                          ctx->stream));
+            dev[k] = stage + (size_t)k * ctx->N;
+        }
+    }
+    RLB_CUDA(ctx, rlb::launch_init(ctx->fp32, ctx->N, ctx->ps, dev[0], dev[1], dev[2], dev[3], dev[4],
+                                   ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur], ctx->prev, ctx->d_status,
+                                   ctx->stream));
+    ctx->launches += 1;
+    return check_device_status(ctx, RLB_E_INVALID);
+}
+
+rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    if (nsteps < 0) return fail(ctx, RLB_E_INVALID, "nsteps must be >= 0");
+    RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    for (long long k = 0; k < nsteps; ++k) {
+        const int c = ctx->cur, o = 1 - c;
+        cudaError_t e;
+        if (ctx->fp32)
+            e = rlb::launch_step_f32(ctx->sp, ctx->dim, ctx->opt.euler_mode, (const float *)ctx->fbuf[c],
+                                     (const float *)ctx->hbuf[c], (float *)ctx->fbuf[o], (float *)ctx->hbuf[o],
+                                     (float *)ctx->prev, ctx->stream);
+        else
+            e = rlb::launch_step_f64(ctx->sp, ctx->dim, ctx->opt.euler_mode, (const double *)ctx->fbuf[c],
+                                     (const double *)ctx->hbuf[c], (double *)ctx->fbuf[o],
+                                     (double *)ctx->hbuf[o], (double *)ctx->prev, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel launch");
+        ctx->launches += 1;
+        ctx->cur = o;
+    }
+    return check_device_status(ctx, RLB_E_NONPHYSICAL);
+}
+
+rlb_status rlb_macroscopic(rlb_ctx *ctx, double *out, int on_device)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    if (!out) return fail(ctx, RLB_E_INVALID, "out is NULL");
+    RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    double *dst = on_device ? out : (double *)ctx->fbuf[1 - ctx->cur];   // 48 N bytes of staging
+    RLB_CUDA(ctx, rlb::launch_macro(ctx->fp32, ctx->N, ctx->ps, ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur],
+                                    dst, ctx->d_status, ctx->stream));
+    ctx->launches += 1;
+    if (!on_device)
+        RLB_CUDA(ctx, cudaMemcpyAsync(out, dst, 6 * sizeof(double) * (size_t)ctx->N, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    return check_device_status(ctx, RLB_E_NONPHYSICAL);
+}
+
+rlb_status rlb_conserved_totals(rlb_ctx *ctx, double *out)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    if (!out) return fail(ctx, RLB_E_INVALID, "out is NULL");
+    RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    RLB_CUDA(ctx, rlb::launch_totals(ctx->fp32, ctx->N, ctx->ps, ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur],
+                                     ctx->d_partial, ctx->d_tot, ctx->stream));
+    ctx->launches += 2;
+    RLB_CUDA(ctx, cudaMemcpyAsync(ctx->h_tot, ctx->d_tot, 5 * sizeof(double), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < 5; ++k) out[k] = ctx->h_tot[k];
+    return RLB_OK;
+}
+
+size_t rlb_state_bytes(const rlb_ctx *ctx)
+{
+    return ctx ? (size_t)43 * ctx->N * ctx->esize : 0;
+}
+
+static rlb_status copy_state(rlb_ctx *ctx, void *buf, size_t bytes, bool out)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    if (!buf) return fail(ctx, RLB_E_INVALID, "buffer is NULL");
+    if (bytes != rlb_state_bytes(ctx)) return fail(ctx, RLB_E_INVALID, "buffer size must equal rlb_state_bytes");
+    RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    const size_t w = (size_t)ctx->N * ctx->esize, pitch = (size_t)ctx->ps * ctx->esize;
+    char *host = (char *)buf;
+    void *dev[3] = {ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur], ctx->prev};
+    const int rows[3] = {19, 19, 5};
+    size_t hoff = 0;
+    for (int k = 0; k < 3; ++k) {
+        if (out)
+            RLB_CUDA(ctx, cudaMemcpy2DAsync(host + hoff, w, dev[k], pitch, w, rows[k], cudaMemcpyDefault,
+                                            ctx->stream));
+        else
+            RLB_CUDA(ctx, cudaMemcpy2DAsync(dev[k], pitch, host + hoff, w, w, rows[k], cudaMemcpyDefault,
+                                            ctx->stream));
+        hoff += w * rows[k];
+    }
+    RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RLB_OK;
+}
+
+rlb_status rlb_get_state(rlb_ctx *ctx, void *buf, size_t bytes, int on_device)
+{
+    (void)on_device;   // cudaMemcpyDefault resolves host and device pointers (UVA)
+    return copy_state(ctx, buf, bytes, true);
+}
+
+rlb_status rlb_set_state(rlb_ctx *ctx, const void *buf, size_t bytes, int on_device)
+{
+    (void)on_device;
+    return copy_state(ctx, const_cast<void *>(buf), bytes, false);
+}
+
+rlb_status rlb_set_stream(rlb_ctx *ctx, void *cuda_stream)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    ctx->stream = (cudaStream_t)cuda_stream;
+    ctx->opt.cuda_stream = cuda_stream;
+    return RLB_OK;
+}
+
+long long rlb_launch_count(const rlb_ctx *ctx)
+{
+    return ctx ? ctx->launches : 0;
+}
+
+void rlb_destroy(rlb_ctx *ctx)
+{
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    if (ctx->block) cudaFree(ctx->block);
+    if (ctx->h_status) cudaFreeHost(ctx->h_status);
+    delete ctx;
+}
+
+const char *rlb_last_error(const rlb_ctx *ctx)
+{
+    return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+const char *rlb_status_string(int status)
+{
+    switch (status) {
+    case RLB_OK: return "RLB_OK";
+    case RLB_E_INVALID: return "RLB_E_INVALID";
+    case RLB_E_NOMEM: return "RLB_E_NOMEM";
+    case RLB_E_CUDA: return "RLB_E_CUDA";
+    case RLB_E_UNSTABLE: return "RLB_E_UNSTABLE";
+    case RLB_E_NONPHYSICAL: return "RLB_E_NONPHYSICAL";
+    case RLB_E_TIMEOUT: return "RLB_E_TIMEOUT";
+    default: return "RLB_E_UNKNOWN";
+    }
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+// rlb_device.cuh -- per-cell physics of the ultra-relativistic lattice
+// Boltzmann step (Mohseni, Mendoza, Succi, Herrmann, arXiv:1302.1125) as
+// device functions: lattice constants, moments, Landau-frame recovery,
+// equilibria, relaxation time, minmod streaming.
+//
+// Lattice units: delta x = 1, c = k_B = 1, nu = sqrt(13) so c_a = 1 and the
+// lattice velocities are the integer vectors of Eq. 42.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace rlb {
+
+// ---------------------------------------------------------------------------
+// Lattice constants (Sec. II.A, Eqs. 42-46 and 59-60), nu = sqrt(13)
+// ---------------------------------------------------------------------------
+constexpr double kXi0 = 1.44115338424578420134928;      // c_t/c_0 = sqrt(27)/nu
+constexpr double kXi0Sq = 27.0 / 13.0;
+constexpr double kC0Ct = 0.693888666488710911760766;    // c_0/c_t
+constexpr double kOmegaC = 2.50185116648837831287298;   // (c_0/c_t) nu = 13/sqrt(27)
+constexpr double kFourOverXi0 = 2.77555466595484364704306;
+constexpr double kPi2Over16 = 0.616850275068084913677156;  // 1 / (d_G / pi^2), d_G = 16
+constexpr double kSMin = 1e-3;  // floor of 4 - ln(lambda) in the entropy density
+
+// weights of f (Eqs. 43-45; independent of nu) and of h (Eqs. 59-60, c_a = 1)
+constexpr double kW[3] = {-539.0 / 676.0, 99.0 / 338.0, 9.0 / 2704.0};
+constexpr double kWh[3] = {0.1, 6.0 / 35.0 - 1.0 / 42.0, 1.0 / 84.0 - 3.0 / 280.0};
+
+// integer velocity components c_i (c_a = 1; the diagonals carry 2 c_a)
+struct Dir {
+    int x, y, z;
+};
+constexpr Dir kDir[19] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0, -1, 0},
+                          {0, 0, 1},   {0, 0, -1},  {2, 2, 0},   {2, -2, 0},  {-2, 2, 0},
+                          {-2, -2, 0}, {2, 0, 2},   {2, 0, -2},  {-2, 0, 2},  {-2, 0, -2},
+                          {0, 2, 2},   {0, 2, -2},  {0, -2, 2},  {0, -2, -2}};
+
+template <int I, int A>
+__host__ __device__ constexpr int cdir()
+{
+    return A == 0 ? kDir[I].x : (A == 1 ? kDir[I].y : kDir[I].z);
+}
+template <int I>
+__host__ __device__ constexpr int shell()
+{
+    return I == 0 ? 0 : (I <= 6 ? 1 : 2);
+}
+
+enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INLET = 2 };
+enum { ST_NONPHYSICAL = 1 };
+
+// ---------------------------------------------------------------------------
+// Macroscopic state and recovery (Sec. II: T^{0 mu} plus eps = 3P, Eq. 38)
+// ---------------------------------------------------------------------------
+struct Macro {
+    double P, ux, uy, uz, n;   // u' = gamma u (spatial part of U^mu)
+};
+
+// Landau frame for eps = 3P: E = 4 P gamma^2 - P, M = 4 P gamma^2 u.  The
+// eigenvalue is eps = 3 (E^2 - |M|^2) / (E + sqrt(4 E^2 - 3 |M|^2)); then
+// gamma^2 = (E + P) / (4 P), u' = M / (4 P gamma), n = N^0 / gamma.
+__host__ __device__ __forceinline__ bool recover(double E, double Mx, double My, double Mz, double N0,
+                                        Macro &m)
+{
+    const double M2 = Mx * Mx + My * My + Mz * Mz;
+    const double D = E * E - M2;
+    const double eps = 3.0 * D / (E + sqrt(4.0 * E * E - 3.0 * M2));
+    const double P = eps * (1.0 / 3.0);
+    const double g2 = (E + P) / (4.0 * P);
+    const double g = sqrt(g2);
+    const double s = 1.0 / (4.0 * P * g);
+    m.P = P;
+    m.ux = Mx * s;
+    m.uy = My * s;
+    m.uz = Mz * s;
+    m.n = N0 / g;
+    return (E > 0.0) && (D > 0.0) && isfinite(m.n) && isfinite(s);
+}
+
+// tau from eta/s (Eq. 41 with s = n (4 - ln lambda), lambda = n / n_eq,
+// n_eq = 16 T^3 / pi^2, T = P/n, Sec. III): tau = 1/2 + nu^2 (eta/s)(4 - ln lambda)/(4 T)
+__device__ __forceinline__ double tau_of(double P, double n, double eta_over_s)
+{
+    const double T = P / n;
+    const double lam = n * kPi2Over16 / (T * T * T);
+    const double sfac = fmax(4.0 - log(lam), kSMin);
+    return 0.5 + 13.0 * eta_over_s * sfac / (4.0 * T);
+}
+
+// ---------------------------------------------------------------------------
+// Equilibria as coefficient sets.  With integer c_i:
+//   f_i^eq = w_i [K0 + sum_a c_a Kb_a + sum_a c_a^2 Kd_a + sum_{a<b} c_a c_b Ko_ab]
+// is the second-order polynomial in u' whose lattice moments give
+// T^{mu nu} = 4 P U^mu U^nu - P eta^{mu nu} (Eq. 36): with A = P / sigma2 =
+// 13 P / 9, K0 = A (1 - 16/15 |u'|^2), Kb = A (4 gamma / xi0) u',
+// Kd = A (52/15) u'^2, Ko = 13 A u'_a u'_b.
+//   h_i^eq = w'_i n gamma (c0/ct + 3 c.u + 9/2 (c.u)^2 - 3/2 |u|^2)  (Eq. 58)
+// gives H0 = B (c0/ct - 3/2 |u|^2), Hb = 3 B u, Hd = 9/2 B u^2,
+// Ho = 9 B u_a u_b with B = n gamma.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Coef {
+    R K0, Kb[3], Kd[3], Ko[3];   // Ko order: xy, xz, yz
+};
+
+__host__ __device__ __forceinline__ void coef_f(const Macro &m, Coef<double> &k)
+{
+    const double u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    const double g = sqrt(1.0 + u2);
+    const double A = m.P * (13.0 / 9.0);
+    const double b = A * kFourOverXi0 * g;
+    const double d = A * (52.0 / 15.0);
+    const double o = A * 13.0;
+    k.K0 = A * (1.0 - (16.0 / 15.0) * u2);
+    k.Kb[0] = b * m.ux;
+    k.Kb[1] = b * m.uy;
+    k.Kb[2] = b * m.uz;
+    k.Kd[0] = d * m.ux * m.ux;
+    k.Kd[1] = d * m.uy * m.uy;
+    k.Kd[2] = d * m.uz * m.uz;
+    k.Ko[0] = o * m.ux * m.uy;
+    k.Ko[1] = o * m.ux * m.uz;
+    k.Ko[2] = o * m.uy * m.uz;
+}
+
+__host__ __device__ __forceinline__ void coef_h(const Macro &m, Coef<double> &k)
+{
+    const double u2p = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
+    const double g = sqrt(1.0 + u2p);
+    const double ig = 1.0 / g;
+    const double ux = m.ux * ig, uy = m.uy * ig, uz = m.uz * ig;
+    const double B = m.n * g;
+    k.K0 = B * (kC0Ct - 1.5 * (ux * ux + uy * uy + uz * uz));
+    k.Kb[0] = 3.0 * B * ux;
+    k.Kb[1] = 3.0 * B * uy;
+    k.Kb[2] = 3.0 * B * uz;
+    k.Kd[0] = 4.5 * B * ux * ux;
+    k.Kd[1] = 4.5 * B * uy * uy;
+    k.Kd[2] = 4.5 * B * uz * uz;
+    k.Ko[0] = 9.0 * B * ux * uy;
+    k.Ko[1] = 9.0 * B * ux * uz;
+    k.Ko[2] = 9.0 * B * uy * uz;
+}
+
+// 2 k(t) - k(t - dt), the extrapolated equilibrium of Eq. 57
+template <typename R>
+__host__ __device__ __forceinline__ Coef<R> extrapolate(const Coef<double> &a, const Coef<double> &b)
+{
+    Coef<R> k;
+    k.K0 = R(2.0 * a.K0 - b.K0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        k.Kb[j] = R(2.0 * a.Kb[j] - b.Kb[j]);
+        k.Kd[j] = R(2.0 * a.Kd[j] - b.Kd[j]);
+        k.Ko[j] = R(2.0 * a.Ko[j] - b.Ko[j]);
+    }
+    return k;
+}
+
+template <typename R>
+__host__ __device__ __forceinline__ Coef<R> cast_coef(const Coef<double> &a)
+{
+    Coef<R> k;
+    k.K0 = R(a.K0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        k.Kb[j] = R(a.Kb[j]);
+        k.Kd[j] = R(a.Kd[j]);
+        k.Ko[j] = R(a.Ko[j]);
+    }
+    return k;
+}
+
+// evaluate population I of an equilibrium from its coefficients; only the
+// terms with nonzero lattice components are generated
+template <int I, bool IS_F, typename R>
+__host__ __device__ __forceinline__ R eq_pop(const Coef<R> &k)
+{
+    constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+    R s = k.K0;
+    if constexpr (cx != 0) s += R(cx) * k.Kb[0] + R(cx * cx) * k.Kd[0];
+    if constexpr (cy != 0) s += R(cy) * k.Kb[1] + R(cy * cy) * k.Kd[1];
+    if constexpr (cz != 0) s += R(cz) * k.Kb[2] + R(cz * cz) * k.Kd[2];
+    if constexpr (cx * cy != 0) s += R(cx * cy) * k.Ko[0];
+    if constexpr (cx * cz != 0) s += R(cx * cz) * k.Ko[1];
+    if constexpr (cy * cz != 0) s += R(cy * cz) * k.Ko[2];
+    constexpr double w = IS_F ? kW[shell<I>()] : kWh[shell<I>()];
+    return R(w) * s;
+}
+
+// ---------------------------------------------------------------------------
+// Streaming (Eqs. 47-53) and the minmod limiter
+// ---------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ R minmod(R a, R b)
+{
+    const R m = fmin(fabs(a), fabs(b));
+    return (a > R(0) && b > R(0)) ? m : ((a < R(0) && b < R(0)) ? -m : R(0));
+}
+
+// Neighbour map of one axis: linear offsets of the cells at d = -2, -1, +1, +2
+// after the boundary rule, and a mask of inlet ghost cells.
+struct AxisNbr {
+    int off[4];
+    unsigned ghost;
+};
+
+__device__ __forceinline__ AxisNbr axis_map(int c, int n, int stride, int lo, int hi)
+{
+    AxisNbr r;
+    r.ghost = 0u;
+    const int ds[4] = {-2, -1, 1, 2};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        int cc = c + ds[k];
+        if (cc < 0 || cc >= n) {
+            const int bc = cc < 0 ? lo : hi;
+            if (bc == BC_PERIODIC) {
+                cc %= n;
+                if (cc < 0) cc += n;
+            } else if (bc == BC_OUTFLOW) {
+                cc = cc < 0 ? 0 : n - 1;
+            } else {
+                r.ghost |= 1u << k;
+                cc = c;
+            }
+        }
+        r.off[k] = (cc - c) * stride;
+    }
+    return r;
+}
+
+}  // namespace rlb

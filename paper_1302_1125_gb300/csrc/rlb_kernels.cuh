@@ -1,0 +1,199 @@
+// rlb_kernels.cuh -- kernels of the fused RLB time step.
+//
+// One thread updates one cell: it reads the 19 + 19 local populations,
+// forms the moments and the Landau-frame macroscopic state of time t,
+// evaluates the extrapolated equilibria 2 f^eq(t) - f^eq(t - dt) from the
+// current and the stored previous macroscopic state, streams every
+// population with the minmod flux difference of its own neighbours
+// (plus the bulk Laplacian for f), applies the implicit update of Eq. 57
+// and writes the populations of t + dt and the macroscopic state of t.
+#pragma once
+
+#include <utility>
+
+#include "rlb_device.cuh"
+#include "rlb_internal.h"
+
+namespace rlb {
+
+template <int... Is, typename F>
+__device__ __forceinline__ void for_pops(std::integer_sequence<int, Is...>, F &&fn)
+{
+    (fn(std::integral_constant<int, Is>{}), ...);
+}
+#define RLB_POPS std::make_integer_sequence<int, 19>{}
+
+template <typename T>
+__device__ __forceinline__ T ldg(const T *p)
+{
+    return __ldg(p);
+}
+
+// value of a neighbour (slot k of the axis map) or the inlet ghost value
+template <typename T>
+__device__ __forceinline__ T nbr(const T *q, int idx, const AxisNbr &a, int k, T ghost)
+{
+    return ((a.ghost >> k) & 1u) ? ghost : ldg(q + idx + a.off[k]);
+}
+
+// Streaming increment of one population along axis A: minus dt (c0/ct) times
+// the conservative minmod flux difference h^a(x) - h^a(x - e_a) (Eqs. 47-53),
+// and, for f with i != 0, the central second difference for the bulk term.
+template <typename T, bool IS_F, int I, int A>
+__device__ __forceinline__ void axis_terms(const T *q, int idx, const AxisNbr &an, T qc, T ghost,
+                                           T k1, T k2, T hl, T &inc, T &lap)
+{
+    constexpr int c = cdir<I, A>();
+    constexpr bool need_lap = IS_F && I != 0;
+    if constexpr (c > 0) {
+        const T qm2 = nbr(q, idx, an, 0, ghost);
+        const T qm1 = nbr(q, idx, an, 1, ghost);
+        const T qp1 = nbr(q, idx, an, 2, ghost);
+        const T d0 = qm1 - qm2, d1 = qc - qm1, d2 = qp1 - qc;
+        const T D = d1 + hl * (minmod(d2, d1) - minmod(d1, d0));
+        inc -= (c == 1 ? k1 : k2) * D;
+        if constexpr (need_lap) lap += (qp1 - qc) - d1;
+    } else if constexpr (c < 0) {
+        const T qm1 = nbr(q, idx, an, 1, ghost);
+        const T qp1 = nbr(q, idx, an, 2, ghost);
+        const T qp2 = nbr(q, idx, an, 3, ghost);
+        const T e0 = qc - qm1, e1 = qp1 - qc, e2 = qp2 - qp1;
+        const T D = e1 - hl * (minmod(e1, e2) - minmod(e0, e1));
+        inc += (c == -1 ? k1 : k2) * D;
+        if constexpr (need_lap) lap += e1 - e0;
+    } else if constexpr (need_lap) {
+        const T qm1 = nbr(q, idx, an, 1, ghost);
+        const T qp1 = nbr(q, idx, an, 2, ghost);
+        lap += (qp1 - qc) - (qc - qm1);
+    }
+}
+
+// f + streaming (+ bulk) for population I: the explicit part of Eq. 57
+template <typename T, int DIM, bool IS_F, int I>
+__device__ __forceinline__ T streamed(const T *q, int idx, const AxisNbr (&am)[3], T qc, T ghost,
+                                      T k1, T k2, T hl, T kbulk)
+{
+    T inc = T(0), lap = T(0);
+    axis_terms<T, IS_F, I, 0>(q, idx, am[0], qc, ghost, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 1) axis_terms<T, IS_F, I, 1>(q, idx, am[1], qc, ghost, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 2) axis_terms<T, IS_F, I, 2>(q, idx, am[2], qc, ghost, k1, k2, hl, inc, lap);
+    if constexpr (IS_F && I != 0) inc += kbulk * lap;
+    return qc + inc;
+}
+
+template <typename T>
+__device__ __forceinline__ void flag(const StepParams &p, unsigned bits)
+{
+    atomicOr(p.status, bits);
+}
+
+template <typename T, int DIM, bool EULER>
+__global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *__restrict__ f,
+                                                   const T *__restrict__ h, T *__restrict__ fo,
+                                                   T *__restrict__ ho, T *__restrict__ prev)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const int idx = x + p.nx * (y + p.ny * z);
+    const long long ps = p.ps;
+
+    AxisNbr am[3];
+    am[0] = axis_map(x, p.nx, 1, p.bc_lo[0], p.bc_hi[0]);
+    if (DIM > 1) am[1] = axis_map(y, p.ny, p.nx, p.bc_lo[1], p.bc_hi[1]);
+    if (DIM > 2) am[2] = axis_map(z, p.nz, p.nx * p.ny, p.bc_lo[2], p.bc_hi[2]);
+
+    const T k1 = T(p.k1), k2 = T(p.k2), hl = T(p.half_lim), kbulk = T(p.kbulk);
+
+    if constexpr (!EULER) {
+        // moments of f(t), h(t) at the cell (Eq. 36 with p_i^0 = xi0)
+        T fl[19], hq[19];
+        double sf = 0.0, sh = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+        for_pops(RLB_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            fl[I] = ldg(f + I * ps + idx);
+            hq[I] = ldg(h + I * ps + idx);
+            const double fv = double(fl[I]);
+            sf += fv;
+            sh += double(hq[I]);
+            if constexpr (cdir<I, 0>() != 0) mx += double(cdir<I, 0>()) * fv;
+            if constexpr (cdir<I, 1>() != 0) my += double(cdir<I, 1>()) * fv;
+            if constexpr (cdir<I, 2>() != 0) mz += double(cdir<I, 2>()) * fv;
+        });
+        Macro mt;
+        const bool ok = recover(kXi0Sq * sf, kXi0 * mx, kXi0 * my, kXi0 * mz, kXi0 * sh, mt);
+        if (!ok) flag<T>(p, ST_NONPHYSICAL);
+        const double tau = p.tau_override > 0.0 ? p.tau_override : tau_of(mt.P, mt.n, p.eta_over_s);
+        const double omega = p.kw / tau;
+        const T om = T(omega), inv = T(1.0 / (1.0 + omega));
+
+        Macro mp;
+        mp.P = double(prev[0 * ps + idx]);
+        mp.ux = double(prev[1 * ps + idx]);
+        mp.uy = double(prev[2 * ps + idx]);
+        mp.uz = double(prev[3 * ps + idx]);
+        mp.n = double(prev[4 * ps + idx]);
+        Coef<double> a, b;
+        coef_f(mt, a);
+        coef_f(mp, b);
+        const Coef<T> kf = extrapolate<T>(a, b);
+        coef_h(mt, a);
+        coef_h(mp, b);
+        const Coef<T> kh = extrapolate<T>(a, b);
+
+        for_pops(RLB_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const T pre = streamed<T, DIM, true, I>(f + I * ps, idx, am, fl[I], T(p.ghost_f[I]), k1,
+                                                    k2, hl, kbulk);
+            fo[I * ps + idx] = (pre + om * eq_pop<I, true>(kf)) * inv;
+        });
+        for_pops(RLB_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const T pre = streamed<T, DIM, false, I>(h + I * ps, idx, am, hq[I], T(p.ghost_h[I]),
+                                                     k1, k2, hl, kbulk);
+            ho[I * ps + idx] = (pre + om * eq_pop<I, false>(kh)) * inv;
+        });
+        prev[0 * ps + idx] = T(mt.P);
+        prev[1 * ps + idx] = T(mt.ux);
+        prev[2 * ps + idx] = T(mt.uy);
+        prev[3 * ps + idx] = T(mt.uz);
+        prev[4 * ps + idx] = T(mt.n);
+    } else {
+        // Euler mode (Sec. III): f, h <- equilibria of the streamed state
+        double sf = 0.0, sh = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
+        for_pops(RLB_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const T qc = ldg(f + I * ps + idx);
+            const double fv = double(streamed<T, DIM, true, I>(f + I * ps, idx, am, qc,
+                                                               T(p.ghost_f[I]), k1, k2, hl, kbulk));
+            sf += fv;
+            if constexpr (cdir<I, 0>() != 0) mx += double(cdir<I, 0>()) * fv;
+            if constexpr (cdir<I, 1>() != 0) my += double(cdir<I, 1>()) * fv;
+            if constexpr (cdir<I, 2>() != 0) mz += double(cdir<I, 2>()) * fv;
+            const T qh = ldg(h + I * ps + idx);
+            sh += double(streamed<T, DIM, false, I>(h + I * ps, idx, am, qh, T(p.ghost_h[I]), k1, k2,
+                                                    hl, kbulk));
+        });
+        Macro mt;
+        const bool ok = recover(kXi0Sq * sf, kXi0 * mx, kXi0 * my, kXi0 * mz, kXi0 * sh, mt);
+        if (!ok) flag<T>(p, ST_NONPHYSICAL);
+        Coef<double> a;
+        coef_f(mt, a);
+        const Coef<T> kf = cast_coef<T>(a);
+        coef_h(mt, a);
+        const Coef<T> kh = cast_coef<T>(a);
+        for_pops(RLB_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            fo[I * ps + idx] = eq_pop<I, true>(kf);
+            ho[I * ps + idx] = eq_pop<I, false>(kh);
+        });
+        prev[0 * ps + idx] = T(mt.P);
+        prev[1 * ps + idx] = T(mt.ux);
+        prev[2 * ps + idx] = T(mt.uy);
+        prev[3 * ps + idx] = T(mt.uz);
+        prev[4 * ps + idx] = T(mt.n);
+    }
+}
+
+}  // namespace rlb

@@ -1,0 +1,292 @@
+"""Thin ctypes binding of librlb (include/rlb.h).
+
+Argument marshalling only: every step of the method runs in the CUDA
+kernels of librlb.so.  The functions below carry the names of the C ABI;
+``Grid`` wraps one context for convenience.  Device buffers are torch CUDA
+tensors (PyTorch provides device memory and streams), host buffers are
+numpy arrays or CPU tensors.  There is no CPU fallback: if librlb.so is
+missing or no GPU is present the calls fail with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librlb.so")
+
+RLB_OK, RLB_E_INVALID, RLB_E_NOMEM, RLB_E_CUDA = 0, -1, -2, -3
+RLB_E_UNSTABLE, RLB_E_NONPHYSICAL, RLB_E_TIMEOUT = -4, -5, -6
+LIMITER_MINMOD, LIMITER_NONE = 0, 1
+BC_PERIODIC, BC_OUTFLOW, BC_INLET = 0, 1, 2
+FP64, FP32_STORAGE = 0, 1
+Q = 19
+
+
+class rlb_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3),
+                ("inlet_n", C.c_double), ("inlet_T", C.c_double), ("inlet_u", C.c_double * 3)]
+
+
+class rlb_options(C.Structure):
+    _fields_ = [("dt_over_dx", C.c_double), ("tau_override", C.c_double),
+                ("alpha_override", C.c_double), ("euler_mode", C.c_int),
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class RLBError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{status_string(status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Load librlb.so (built in-tree by paper_1302_1125_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run `python -m paper_1302_1125_gb300.build` "
+                               "(the CUDA library is required, there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        ctxp = C.c_void_p
+        L.rlb_default_options.argtypes = [C.POINTER(rlb_options)]
+        L.rlb_default_options.restype = None
+        L.rlb_check_config.argtypes = [C.POINTER(rlb_grid), C.c_int, C.c_double, C.c_double, C.c_int,
+                                       C.POINTER(rlb_options)]
+        L.rlb_check_config.restype = C.c_int
+        L.rlb_create.argtypes = [C.POINTER(rlb_grid), C.c_int, C.c_double, C.c_double, C.c_int,
+                                 C.POINTER(rlb_options), C.POINTER(ctxp)]
+        L.rlb_create.restype = C.c_int
+        L.rlb_init.argtypes = [ctxp, vp, vp, vp, vp, vp, C.c_int]
+        L.rlb_init.restype = C.c_int
+        L.rlb_step.argtypes = [ctxp, C.c_longlong]
+        L.rlb_step.restype = C.c_int
+        L.rlb_macroscopic.argtypes = [ctxp, vp, C.c_int]
+        L.rlb_macroscopic.restype = C.c_int
+        L.rlb_conserved_totals.argtypes = [ctxp, dp]
+        L.rlb_conserved_totals.restype = C.c_int
+        L.rlb_state_bytes.argtypes = [ctxp]
+        L.rlb_state_bytes.restype = C.c_size_t
+        L.rlb_get_state.argtypes = [ctxp, vp, C.c_size_t, C.c_int]
+        L.rlb_get_state.restype = C.c_int
+        L.rlb_set_state.argtypes = [ctxp, vp, C.c_size_t, C.c_int]
+        L.rlb_set_state.restype = C.c_int
+        L.rlb_set_stream.argtypes = [ctxp, vp]
+        L.rlb_set_stream.restype = C.c_int
+        L.rlb_launch_count.argtypes = [ctxp]
+        L.rlb_launch_count.restype = C.c_longlong
+        L.rlb_destroy.argtypes = [ctxp]
+        L.rlb_destroy.restype = None
+        L.rlb_last_error.argtypes = [ctxp]
+        L.rlb_last_error.restype = C.c_char_p
+        L.rlb_status_string.argtypes = [C.c_int]
+        L.rlb_status_string.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def status_string(status: int) -> str:
+    return lib().rlb_status_string(int(status)).decode()
+
+
+def last_error(ctx=None) -> str:
+    return lib().rlb_last_error(ctx).decode()
+
+
+def _check(status: int, ctx=None):
+    if status != RLB_OK:
+        raise RLBError(status, last_error(ctx))
+
+
+def make_grid(nx, ny=1, nz=1, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
+              bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0))):
+    n, T, u = inlet
+    return rlb_grid(int(nx), int(ny), int(nz), (C.c_int * 3)(*bc_lo), (C.c_int * 3)(*bc_hi),
+                    float(n), float(T), (C.c_double * 3)(*u))
+
+
+def make_options(dt_over_dx=0.25, tau_override=0.0, alpha_override=-1.0, euler_mode=0,
+                 precision=FP64, cuda_stream=None):
+    return rlb_options(float(dt_over_dx), float(tau_override), float(alpha_override),
+                       int(euler_mode), int(precision), cuda_stream)
+
+
+def rlb_check_config(grid, Q, eta_over_s, zeta_over_s, limiter, opts) -> int:
+    return lib().rlb_check_config(C.byref(grid), int(Q), float(eta_over_s), float(zeta_over_s),
+                                  int(limiter), C.byref(opts) if opts is not None else None)
+
+
+def rlb_create(grid, Q, eta_over_s, zeta_over_s, limiter, opts):
+    ctx = C.c_void_p()
+    st = lib().rlb_create(C.byref(grid), int(Q), float(eta_over_s), float(zeta_over_s),
+                          int(limiter), C.byref(opts) if opts is not None else None, C.byref(ctx))
+    _check(st)
+    return ctx
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _current_stream():
+    try:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return None
+
+
+def _as_f64(a, N):
+    """(pointer, on_device, keepalive) for an N-vector of float64"""
+    if hasattr(a, "is_cuda"):
+        torch = _torch()
+        t = a.reshape(-1).to(torch.float64).contiguous()
+        if t.numel() != N:
+            raise ValueError(f"field has {t.numel()} values, expected {N}")
+        if t.is_cuda:
+            return t.data_ptr(), 1, t
+        arr = t.numpy()
+    else:
+        arr = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (N,)))
+    return arr.ctypes.data, 0, arr
+
+
+def rlb_init(ctx, n, T, ux, uy, uz, N):
+    ptrs, keep = [], []
+    ondev = None
+    for a in (n, T, ux, uy, uz):
+        p, d, k = _as_f64(a, N)
+        ondev = d if ondev is None else ondev
+        if d != ondev:
+            raise ValueError("all fields must be on the same side (host or device)")
+        ptrs.append(p)
+        keep.append(k)
+    _check(lib().rlb_init(ctx, *ptrs, ondev), ctx)
+
+
+def rlb_step(ctx, nsteps: int):
+    _check(lib().rlb_step(ctx, int(nsteps)), ctx)
+
+
+def rlb_macroscopic(ctx, out, on_device: int):
+    ptr = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+    _check(lib().rlb_macroscopic(ctx, ptr, int(on_device)), ctx)
+
+
+def rlb_conserved_totals(ctx) -> np.ndarray:
+    out = np.zeros(5)
+    _check(lib().rlb_conserved_totals(ctx, out.ctypes.data_as(C.POINTER(C.c_double))), ctx)
+    return out
+
+
+def rlb_state_bytes(ctx) -> int:
+    return int(lib().rlb_state_bytes(ctx))
+
+
+def rlb_get_state(ctx, buf, on_device: int):
+    ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+    _check(lib().rlb_get_state(ctx, ptr, rlb_state_bytes(ctx), int(on_device)), ctx)
+
+
+def rlb_set_state(ctx, buf, on_device: int):
+    ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
+    _check(lib().rlb_set_state(ctx, ptr, rlb_state_bytes(ctx), int(on_device)), ctx)
+
+
+def rlb_set_stream(ctx, stream):
+    _check(lib().rlb_set_stream(ctx, stream), ctx)
+
+
+def rlb_launch_count(ctx) -> int:
+    return int(lib().rlb_launch_count(ctx))
+
+
+def rlb_destroy(ctx):
+    lib().rlb_destroy(ctx)
+
+
+class Grid:
+    """One simulation context: a grid, its populations and parameters."""
+
+    def __init__(self, nx, ny=1, nz=1, *, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
+                 bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
+                 eta_over_s=0.1, zeta_over_s=0.0, limiter=LIMITER_MINMOD, dt_over_dx=0.25,
+                 tau_override=0.0, alpha_override=-1.0, euler_mode=0, precision=FP64,
+                 stream="current"):
+        self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
+        self.N = self.nx * self.ny * self.nz
+        self.precision = int(precision)
+        s = _current_stream() if stream == "current" else stream
+        self._grid = make_grid(nx, ny, nz, bc_lo, bc_hi, inlet)
+        self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s)
+        self.ctx = rlb_create(self._grid, Q, eta_over_s, zeta_over_s, limiter, self._opts)
+
+    @classmethod
+    def from_workload(cls, w, precision=None, **kw):
+        return cls(w.nx, w.ny, w.nz, bc_lo=w.bc_lo, bc_hi=w.bc_hi, inlet=w.inlet,
+                   eta_over_s=w.eta_over_s, zeta_over_s=w.zeta_over_s, dt_over_dx=w.dt_over_dx,
+                   tau_override=w.tau_override, alpha_override=w.alpha_override,
+                   euler_mode=w.euler_mode,
+                   precision=w.precision if precision is None else precision, **kw)
+
+    def init(self, n, T, ux, uy, uz):
+        rlb_init(self.ctx, n, T, ux, uy, uz, self.N)
+        return self
+
+    def step(self, nsteps=1):
+        rlb_step(self.ctx, nsteps)
+        return self
+
+    def macroscopic(self, device=True):
+        """(6, N) float64: n, e, u_x, u_y, u_z, gamma (torch CUDA tensor or numpy)"""
+        if device:
+            torch = _torch()
+            out = torch.empty((6, self.N), dtype=torch.float64, device="cuda")
+            rlb_macroscopic(self.ctx, out, 1)
+            return out
+        out = np.empty((6, self.N))
+        rlb_macroscopic(self.ctx, out, 0)
+        return out
+
+    def totals(self):
+        return rlb_conserved_totals(self.ctx)
+
+    def state_dtype(self):
+        return np.float32 if self.precision == FP32_STORAGE else np.float64
+
+    def get_state(self):
+        """host numpy copy: (f[19, N], h[19, N], prev[5, N])"""
+        buf = np.empty(43 * self.N, self.state_dtype())
+        rlb_get_state(self.ctx, buf, 0)
+        return buf[:19 * self.N].reshape(19, self.N), buf[19 * self.N:38 * self.N].reshape(19, self.N), \
+            buf[38 * self.N:].reshape(5, self.N)
+
+    def set_state(self, f, h, prev):
+        buf = np.ascontiguousarray(np.concatenate([np.ravel(f), np.ravel(h), np.ravel(prev)]),
+                                   self.state_dtype())
+        rlb_set_state(self.ctx, buf, 0)
+
+    @property
+    def launches(self) -> int:
+        return rlb_launch_count(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            rlb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,108 @@
+"""The C ABI without a GPU: librlb.so builds and loads, exports every entry
+point include/rlb.h declares, and validates configurations on the host
+(rlb_check_config and the argument checks of rlb_create run before any CUDA
+call)."""
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_1302_1125_gb300 import build as B
+from paper_1302_1125_gb300 import rlb
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "rlb.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return rlb.lib()
+
+
+def declared():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"RLB_API[^;(]*?\b(rlb_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_api():
+    names = declared()
+    for must in ("rlb_create", "rlb_init", "rlb_step", "rlb_macroscopic", "rlb_destroy"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.run(["nm", "-D", "--defined-only", rlb.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s(rlb_\w+)", out))
+    missing = [n for n in declared() if n not in exported]
+    assert not missing, missing
+    for n in declared():
+        assert hasattr(lib, n)
+
+
+def test_library_does_not_link_the_oracle():
+    out = subprocess.run(["nm", "-D", rlb.LIB_PATH], capture_output=True, text=True, check=True).stdout
+    assert "orc_" not in out
+
+
+def cfg(**kw):
+    g = dict(nx=64, ny=1, nz=1, bc_lo=(1, 0, 0), bc_hi=(1, 0, 0), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)))
+    o = dict(dt_over_dx=0.25)
+    for k in list(kw):
+        if k in g:
+            g[k] = kw.pop(k)
+        elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision"):
+            o[k] = kw.pop(k)
+    return rlb.make_grid(**g), rlb.make_options(**o), kw
+
+
+@pytest.mark.parametrize("change,expect", [
+    ({}, rlb.RLB_OK),
+    ({"Q": 18}, rlb.RLB_E_INVALID),
+    ({"nx": 0}, rlb.RLB_E_INVALID),
+    ({"nx": 2048, "ny": 2048, "nz": 1024}, rlb.RLB_E_INVALID),
+    ({"eta": -0.1}, rlb.RLB_E_INVALID),
+    ({"zeta": math.nan}, rlb.RLB_E_INVALID),
+    ({"limiter": 7}, rlb.RLB_E_INVALID),
+    ({"precision": 3}, rlb.RLB_E_INVALID),
+    ({"bc_lo": (2, 2, 0)}, rlb.RLB_E_INVALID),
+    ({"bc_lo": (2, 0, 0), "inlet": (1.0, 1.0, (1.0, 0.0, 0.0))}, rlb.RLB_E_INVALID),
+    ({"bc_lo": (2, 0, 0), "inlet": (1.0, 1.0, (0.9, 0.0, 0.0))}, rlb.RLB_OK),
+    ({"dt_over_dx": 0.73}, rlb.RLB_E_UNSTABLE),          # 1-D Courant bound 0.72
+    ({"dt_over_dx": 0.7}, rlb.RLB_OK),
+    ({"ny": 8, "dt_over_dx": 0.37}, rlb.RLB_E_UNSTABLE),  # 2-D bound 0.36
+    ({"alpha_override": 1.0}, rlb.RLB_E_UNSTABLE),       # 2 (c0 nu/ct) dt alpha > 1
+    ({"alpha_override": 0.5}, rlb.RLB_OK),
+    ({"dt_over_dx": -1.0}, rlb.RLB_E_INVALID),
+])
+def test_host_validation(lib, change, expect):
+    change = dict(change)
+    Q = change.pop("Q", 19)
+    eta = change.pop("eta", 0.1)
+    zeta = change.pop("zeta", 0.0)
+    limiter = change.pop("limiter", 0)
+    g, o, rest = cfg(**change)
+    assert not rest
+    assert rlb.rlb_check_config(g, Q, eta, zeta, limiter, o) == expect
+    if expect != rlb.RLB_OK:
+        # rlb_create rejects the same configuration before touching the GPU
+        with pytest.raises(rlb.RLBError) as e:
+            rlb.rlb_create(g, Q, eta, zeta, limiter, o)
+        assert e.value.status == expect
+        assert rlb.last_error() != ""
+
+
+def test_status_strings(lib):
+    assert rlb.status_string(rlb.RLB_E_NONPHYSICAL) == "RLB_E_NONPHYSICAL"
+    assert rlb.status_string(12345) == "RLB_E_UNKNOWN"
+
+
+def test_null_handles_are_rejected(lib):
+    L = rlb.lib()
+    assert L.rlb_step(None, 1) == rlb.RLB_E_INVALID
+    assert L.rlb_init(None, None, None, None, None, None, 0) == rlb.RLB_E_INVALID
+    assert L.rlb_state_bytes(None) == 0
+    L.rlb_destroy(None)
