@@ -38,6 +38,30 @@ BYTES_FP32 = 38 * 4 * 2 + 5 * 4 * 2     # 344
 BYTES_FP64 = 38 * 8 * 2 + 5 * 8 * 2     # 688
 
 
+def csrc_hash() -> str:
+    import hashlib
+    d = os.path.join(ROOT, "paper_1302_1125_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(summary: str, cells: int):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    scaled to `cells`, or None if the kernel sources changed since the capture"""
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("csrc_sha256:",
+                                                                                 "traffic_bytes_per_cell:")))
+    if fields.get("csrc_sha256", "").split()[0:1] != [csrc_hash()]:
+        return None
+    return float(fields["traffic_bytes_per_cell"].split()[0]) * cells
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -295,7 +319,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: 10.2 GB of populations read+written per step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": None,
+                     "frac": achieved / hbm_peak,
+                     "traffic": profiled_traffic("step_kernel_fp32_cloud_3d.md", N),
                      "note": f"{BYTES_FP32} algorithmic bytes per cell update x {N} cells per launch "
                              f"/ CUDA-event time per launch; peak {peak_kind} copy bandwidth"},
         "fp64_form": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,

@@ -141,13 +141,14 @@ void inlet_ghosts(const rlb_grid &g, StepParams &sp)
     m.uy = gam * g.inlet_u[1];
     m.uz = gam * g.inlet_u[2];
     m.n = g.inlet_n;
-    rlb::Coef<double> kf, kh;
-    rlb::coef_f(m, kf);
-    rlb::coef_h(m, kh);
+    rlb::Coef<double> cf, ch;
+    rlb::coef_f(m, cf);
+    rlb::coef_h(m, ch);
+    const rlb::EqW<double> kf = rlb::weigh_f<double>(cf), kh = rlb::weigh_h<double>(ch);
     double *gf = sp.ghost_f, *gh = sp.ghost_h;
     [&]<int... I>(std::integer_sequence<int, I...>) {
-        ((gf[I] = rlb::eq_pop<I, true>(kf)), ...);
-        ((gh[I] = rlb::eq_pop<I, false>(kh)), ...);
+        ((gf[I] = rlb::eq_pop<I>(kf)), ...);
+        ((gh[I] = rlb::eq_pop<I>(kh)), ...);
     }(std::make_integer_sequence<int, 19>{});
 }
 

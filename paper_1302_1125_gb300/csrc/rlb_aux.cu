@@ -26,13 +26,13 @@ __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
     m.n = n[idx];
     Coef<double> a;
     coef_f(m, a);
-    const Coef<T> kf = cast_coef<T>(a);
+    const EqW<T> kf = weigh_f<T>(a);
     coef_h(m, a);
-    const Coef<T> kh = cast_coef<T>(a);
+    const EqW<T> kh = weigh_h<T>(a);
     for_pops(RLB_POPS, [&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        f[I * ps + idx] = eq_pop<I, true>(kf);
-        h[I * ps + idx] = eq_pop<I, false>(kh);
+        f[I * ps + idx] = eq_pop<I>(kf);
+        h[I * ps + idx] = eq_pop<I>(kh);
     });
     prev[0 * ps + idx] = T(m.P);
     prev[1 * ps + idx] = T(m.ux);

@@ -24,8 +24,8 @@ constexpr double kPi2Over16 = 0.616850275068084913677156;  // 1 / (d_G / pi^2), 
 constexpr double kSMin = 1e-3;  // floor of 4 - ln(lambda) in the entropy density
 
 // weights of f (Eqs. 43-45; independent of nu) and of h (Eqs. 59-60, c_a = 1)
-constexpr double kW[3] = {-539.0 / 676.0, 99.0 / 338.0, 9.0 / 2704.0};
-constexpr double kWh[3] = {0.1, 6.0 / 35.0 - 1.0 / 42.0, 1.0 / 84.0 - 3.0 / 280.0};
+constexpr double kW0 = -539.0 / 676.0, kW1 = 99.0 / 338.0, kW2 = 9.0 / 2704.0;
+constexpr double kWh0 = 0.1, kWh1 = 6.0 / 35.0 - 1.0 / 42.0, kWh2 = 1.0 / 84.0 - 3.0 / 280.0;
 
 // integer velocity components c_i (c_a = 1; the diagonals carry 2 c_a)
 struct Dir {
@@ -143,50 +143,87 @@ __host__ __device__ __forceinline__ void coef_h(const Macro &m, Coef<double> &k)
     k.Ko[2] = 9.0 * B * uy * uz;
 }
 
+// An equilibrium with the lattice weights and the diagonal factors 2 and 4
+// folded into its coefficients in double precision, so that a float form
+// rounds each coefficient once instead of carrying a fixed rounding of the
+// weights into every population (that fixed rounding would bias the moment
+// sums, and so the conserved totals, the same way at every step).
+template <typename R>
+struct EqW {
+    R r0;                          // rest:     w0 K0
+    R a0, ab[3], ad[3];            // axis:     w1 K0, w1 Kb, w1 Kd
+    R d0, db[3], dd[3], dk[3];     // diagonal: w2 K0, 2 w2 Kb, 4 w2 Kd, 4 w2 Ko
+};
+
+template <typename R>
+__host__ __device__ __forceinline__ EqW<R> weigh(const Coef<double> &k, double w0, double w1,
+                                                 double w2)
+{
+    EqW<R> e;
+    e.r0 = R(w0 * k.K0);
+    e.a0 = R(w1 * k.K0);
+    e.d0 = R(w2 * k.K0);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        e.ab[j] = R(w1 * k.Kb[j]);
+        e.ad[j] = R(w1 * k.Kd[j]);
+        e.db[j] = R(2.0 * w2 * k.Kb[j]);
+        e.dd[j] = R(4.0 * w2 * k.Kd[j]);
+        e.dk[j] = R(4.0 * w2 * k.Ko[j]);
+    }
+    return e;
+}
+template <typename R>
+__host__ __device__ __forceinline__ EqW<R> weigh_f(const Coef<double> &k)
+{
+    return weigh<R>(k, kW0, kW1, kW2);
+}
+template <typename R>
+__host__ __device__ __forceinline__ EqW<R> weigh_h(const Coef<double> &k)
+{
+    return weigh<R>(k, kWh0, kWh1, kWh2);
+}
+
 // 2 k(t) - k(t - dt), the extrapolated equilibrium of Eq. 57
-template <typename R>
-__host__ __device__ __forceinline__ Coef<R> extrapolate(const Coef<double> &a, const Coef<double> &b)
+__host__ __device__ __forceinline__ Coef<double> extrapolate(const Coef<double> &a,
+                                                             const Coef<double> &b)
 {
-    Coef<R> k;
-    k.K0 = R(2.0 * a.K0 - b.K0);
+    Coef<double> k;
+    k.K0 = 2.0 * a.K0 - b.K0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        k.Kb[j] = R(2.0 * a.Kb[j] - b.Kb[j]);
-        k.Kd[j] = R(2.0 * a.Kd[j] - b.Kd[j]);
-        k.Ko[j] = R(2.0 * a.Ko[j] - b.Ko[j]);
+        k.Kb[j] = 2.0 * a.Kb[j] - b.Kb[j];
+        k.Kd[j] = 2.0 * a.Kd[j] - b.Kd[j];
+        k.Ko[j] = 2.0 * a.Ko[j] - b.Ko[j];
     }
     return k;
 }
 
-template <typename R>
-__host__ __device__ __forceinline__ Coef<R> cast_coef(const Coef<double> &a)
-{
-    Coef<R> k;
-    k.K0 = R(a.K0);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        k.Kb[j] = R(a.Kb[j]);
-        k.Kd[j] = R(a.Kd[j]);
-        k.Ko[j] = R(a.Ko[j]);
-    }
-    return k;
-}
-
-// evaluate population I of an equilibrium from its coefficients; only the
-// terms with nonzero lattice components are generated
-template <int I, bool IS_F, typename R>
-__host__ __device__ __forceinline__ R eq_pop(const Coef<R> &k)
+// population I of an equilibrium: f_i = w_i [K0 + sum_a c_a Kb_a +
+// sum_a c_a^2 Kd_a + sum_{a<b} c_a c_b Ko_ab], with only the terms of the
+// nonzero lattice components generated
+template <int I, typename R>
+__host__ __device__ __forceinline__ R eq_pop(const EqW<R> &e)
 {
     constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
-    R s = k.K0;
-    if constexpr (cx != 0) s += R(cx) * k.Kb[0] + R(cx * cx) * k.Kd[0];
-    if constexpr (cy != 0) s += R(cy) * k.Kb[1] + R(cy * cy) * k.Kd[1];
-    if constexpr (cz != 0) s += R(cz) * k.Kb[2] + R(cz * cz) * k.Kd[2];
-    if constexpr (cx * cy != 0) s += R(cx * cy) * k.Ko[0];
-    if constexpr (cx * cz != 0) s += R(cx * cz) * k.Ko[1];
-    if constexpr (cy * cz != 0) s += R(cy * cz) * k.Ko[2];
-    constexpr double w = IS_F ? kW[shell<I>()] : kWh[shell<I>()];
-    return R(w) * s;
+    constexpr int sh = shell<I>();
+    if constexpr (sh == 0) {
+        return e.r0;
+    } else if constexpr (sh == 1) {
+        constexpr int a = cx != 0 ? 0 : (cy != 0 ? 1 : 2);
+        constexpr int s = cx + cy + cz;   // +1 or -1
+        return s > 0 ? (e.a0 + e.ad[a]) + e.ab[a] : (e.a0 + e.ad[a]) - e.ab[a];
+    } else {
+        constexpr int a = cx != 0 ? 0 : 1;                 // first nonzero axis
+        constexpr int b = cz != 0 ? 2 : 1;                 // second nonzero axis
+        constexpr int ca = a == 0 ? cx : cy, cb = b == 2 ? cz : cy;
+        constexpr int ko = (a == 0 && b == 1) ? 0 : ((a == 0 && b == 2) ? 1 : 2);
+        R v = e.d0 + e.dd[a] + e.dd[b];
+        v = (ca > 0) ? v + e.db[a] : v - e.db[a];
+        v = (cb > 0) ? v + e.db[b] : v - e.db[b];
+        v = (ca * cb > 0) ? v + e.dk[ko] : v - e.dk[ko];
+        return v;
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -126,7 +126,10 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
         if (!ok) flag<T>(p, ST_NONPHYSICAL);
         const double tau = p.tau_override > 0.0 ? p.tau_override : tau_of(mt.P, mt.n, p.eta_over_s);
         const double omega = p.kw / tau;
-        const T om = T(omega), inv = T(1.0 / (1.0 + omega));
+        // f(t+dt) = pre + kappa (G - pre), kappa = omega / (1 + omega): Eq. 57
+        // solved for f(t+dt), in the form whose rounding does not scale the
+        // conserved sums
+        const T kap = T(omega / (1.0 + omega));
 
         Macro mp;
         mp.P = double(prev[0 * ps + idx]);
@@ -137,22 +140,22 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
         Coef<double> a, b;
         coef_f(mt, a);
         coef_f(mp, b);
-        const Coef<T> kf = extrapolate<T>(a, b);
+        const EqW<T> kf = weigh_f<T>(extrapolate(a, b));
         coef_h(mt, a);
         coef_h(mp, b);
-        const Coef<T> kh = extrapolate<T>(a, b);
+        const EqW<T> kh = weigh_h<T>(extrapolate(a, b));
 
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             const T pre = streamed<T, DIM, true, I>(f + I * ps, idx, am, fl[I], T(p.ghost_f[I]), k1,
                                                     k2, hl, kbulk);
-            fo[I * ps + idx] = (pre + om * eq_pop<I, true>(kf)) * inv;
+            fo[I * ps + idx] = pre + kap * (eq_pop<I>(kf) - pre);
         });
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             const T pre = streamed<T, DIM, false, I>(h + I * ps, idx, am, hq[I], T(p.ghost_h[I]),
                                                      k1, k2, hl, kbulk);
-            ho[I * ps + idx] = (pre + om * eq_pop<I, false>(kh)) * inv;
+            ho[I * ps + idx] = pre + kap * (eq_pop<I>(kh) - pre);
         });
         prev[0 * ps + idx] = T(mt.P);
         prev[1 * ps + idx] = T(mt.ux);
@@ -180,13 +183,13 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
         if (!ok) flag<T>(p, ST_NONPHYSICAL);
         Coef<double> a;
         coef_f(mt, a);
-        const Coef<T> kf = cast_coef<T>(a);
+        const EqW<T> kf = weigh_f<T>(a);
         coef_h(mt, a);
-        const Coef<T> kh = cast_coef<T>(a);
+        const EqW<T> kh = weigh_h<T>(a);
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            fo[I * ps + idx] = eq_pop<I, true>(kf);
-            ho[I * ps + idx] = eq_pop<I, false>(kh);
+            fo[I * ps + idx] = eq_pop<I>(kf);
+            ho[I * ps + idx] = eq_pop<I>(kh);
         });
         prev[0 * ps + idx] = T(mt.P);
         prev[1 * ps + idx] = T(mt.ux);
