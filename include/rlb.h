@@ -169,6 +169,37 @@ RLB_API const char *rlb_last_error(const rlb_ctx *ctx);
 /* Name of a status code. */
 RLB_API const char *rlb_status_string(int status);
 
+/* Grid totals without any allocation.  The paper has no counterpart: this
+ * serves callers that cannot call cudaMalloc, for example an application
+ * whose allocator or memory pool reserves all device memory up front, or a
+ * loop that cannot afford the device-wide synchronisation that cudaMalloc
+ * and cudaFree imply.  It computes the same sums as rlb_conserved_totals
+ * (T^00, T^0x, T^0y, T^0z, N^0 over all cells, FP64, same order) from the
+ * caller's buffers: f and h are device pointers to 19 planes each of N
+ * values (float for RLB_FP32_STORAGE, double for RLB_FP64), consecutive
+ * planes plane_stride elements apart (plane_stride >= N, e.g. the compact
+ * layout of rlb_get_state has plane_stride = N); out_device is a
+ * caller-owned device buffer of 5 doubles, written asynchronously on
+ * cuda_stream (NULL = legacy default stream).
+ * The reduction's per-block partial sums live in a fixed device array of
+ * 5 x RLB_NOALLOC_MAX_BLOCKS doubles (47.5 KiB) inside the library, which
+ * every GPU that loads the library holds until the process exits.  The
+ * first call on a device looks up that array's address on the current
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array: calls whose kernels
+ * overlap on the GPU (different streams, no ordering between them) race and
+ * give wrong totals.  Nothing in the array needs clearing between calls;
+ * every slot a call reads it has written first.  Calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ * Errors: RLB_E_INVALID for a NULL pointer, N < 1, N > RLB_NOALLOC_MAX_CELLS,
+ * plane_stride < N or an unknown precision (message in rlb_last_error(NULL));
+ * RLB_E_CUDA if the address lookup or the launch fails. */
+#define RLB_NOALLOC_MAX_BLOCKS 1216
+#define RLB_NOALLOC_MAX_CELLS 2146959360
+RLB_API rlb_status rlb_conserved_totals_noalloc(const void *f, const void *h, int N,
+                                                long long plane_stride, int precision,
+                                                double *out_device, void *cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -167,6 +167,11 @@ rlb_status check_device_status(rlb_ctx *ctx, rlb_status if_bad)
 
 }  // namespace
 
+void rlb::set_thread_error(const char *msg)
+{
+    g_err = msg;
+}
+
 extern "C" {
 
 void rlb_default_options(rlb_options *o)

@@ -37,4 +37,7 @@ int totals_blocks(int N);
 cudaError_t launch_totals(int fp32, int N, long long ps, const void *f, const void *h,
                           double *partial, double *out, cudaStream_t s);
 
+// set the text rlb_last_error(NULL) returns on this thread
+void set_thread_error(const char *msg);
+
 }  // namespace rlb

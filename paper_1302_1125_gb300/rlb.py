@@ -88,6 +88,8 @@ def lib() -> C.CDLL:
         L.rlb_last_error.restype = C.c_char_p
         L.rlb_status_string.argtypes = [C.c_int]
         L.rlb_status_string.restype = C.c_char_p
+        L.rlb_conserved_totals_noalloc.argtypes = [vp, vp, C.c_int, C.c_longlong, C.c_int, vp, vp]
+        L.rlb_conserved_totals_noalloc.restype = C.c_int
         _lib = L
     return _lib
 
@@ -187,6 +189,14 @@ def rlb_conserved_totals(ctx) -> np.ndarray:
     out = np.zeros(5)
     _check(lib().rlb_conserved_totals(ctx, out.ctypes.data_as(C.POINTER(C.c_double))), ctx)
     return out
+
+
+def rlb_conserved_totals_noalloc(f_ptr, h_ptr, N, plane_stride, precision, out_ptr, stream=None):
+    """Allocation-free grid totals from caller device buffers (see rlb.h):
+    f_ptr, h_ptr, out_ptr are device addresses (ints); raises on error."""
+    st = lib().rlb_conserved_totals_noalloc(f_ptr, h_ptr, int(N), int(plane_stride), int(precision),
+                                             out_ptr, stream)
+    _check(st)
 
 
 def rlb_state_bytes(ctx) -> int:
