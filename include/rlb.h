@@ -144,8 +144,13 @@ RLB_API rlb_status rlb_macroscopic(rlb_ctx *ctx, double *out, int on_device);
 RLB_API rlb_status rlb_conserved_totals(rlb_ctx *ctx, double *out);
 
 /* Size in bytes of a checkpoint: 19 N f values, 19 N h values and 5 N
- * previous-level values (P, u'_x, u'_y, u'_z, n), each 8 bytes (RLB_FP64) or
- * 4 bytes (RLB_FP32_STORAGE), in that order, compact planes of N. */
+ * previous-level values, each 8 bytes (RLB_FP64) or 4 bytes
+ * (RLB_FP32_STORAGE), in that order, compact planes of N.  The previous
+ * level is the macroscopic state of the last step, (P, u'_x, u'_y, u'_z, n)
+ * with u' = gamma u, for RLB_FP64, and its raw moment sums (sum_i f_i,
+ * sum_i c_ix f_i, sum_i c_iy f_i, sum_i c_iz f_i, sum_i h_i; c_i the integer
+ * lattice vectors) for RLB_FP32_STORAGE, which keeps the extrapolated
+ * equilibrium's moments exact in float. */
 RLB_API size_t rlb_state_bytes(const rlb_ctx *ctx);
 
 /* Copy the full state out / in (checkpoint and resume).  bytes must equal

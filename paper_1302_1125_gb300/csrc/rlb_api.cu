@@ -284,6 +284,17 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
     sp.tau_override = o.tau_override;
     sp.status = ctx->d_status;
     inlet_ghosts(*grid, sp);
+    sp.f_k1 = float(sp.k1);
+    sp.f_k2 = float(sp.k2);
+    sp.f_half_lim = float(sp.half_lim);
+    sp.f_kw = float(sp.kw);
+    sp.f_kbulk = float(sp.kbulk);
+    sp.f_eta_over_s = float(sp.eta_over_s);
+    sp.f_tau_override = float(sp.tau_override);
+    for (int i = 0; i < 19; ++i) {
+        sp.f_ghost_f[i] = float(sp.ghost_f[i]);
+        sp.f_ghost_h[i] = float(sp.ghost_h[i]);
+    }
     ctx->cur = 0;
     ctx->err = "no error";
     *out = ctx;

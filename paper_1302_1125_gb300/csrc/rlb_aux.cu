@@ -29,16 +29,32 @@ __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
     const EqW<T> kf = weigh_f<T>(a);
     coef_h(m, a);
     const EqW<T> kh = weigh_h<T>(a);
+    double S = 0.0, Vx = 0.0, Vy = 0.0, Vz = 0.0, Sh = 0.0;
     for_pops(RLB_POPS, [&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        f[I * ps + idx] = eq_pop<I>(kf);
-        h[I * ps + idx] = eq_pop<I>(kh);
+        const T fv = eq_pop<I>(kf), hv = eq_pop<I>(kh);
+        f[I * ps + idx] = fv;
+        h[I * ps + idx] = hv;
+        S += double(fv);
+        Sh += double(hv);
+        if constexpr (cdir<I, 0>() != 0) Vx += double(cdir<I, 0>()) * double(fv);
+        if constexpr (cdir<I, 1>() != 0) Vy += double(cdir<I, 1>()) * double(fv);
+        if constexpr (cdir<I, 2>() != 0) Vz += double(cdir<I, 2>()) * double(fv);
     });
-    prev[0 * ps + idx] = T(m.P);
-    prev[1 * ps + idx] = T(m.ux);
-    prev[2 * ps + idx] = T(m.uy);
-    prev[3 * ps + idx] = T(m.uz);
-    prev[4 * ps + idx] = T(m.n);
+    if constexpr (sizeof(T) == 4) {
+        // FP32-storage form: the previous level is the raw moment sums
+        prev[0 * ps + idx] = T(S);
+        prev[1 * ps + idx] = T(Vx);
+        prev[2 * ps + idx] = T(Vy);
+        prev[3 * ps + idx] = T(Vz);
+        prev[4 * ps + idx] = T(Sh);
+    } else {
+        prev[0 * ps + idx] = T(m.P);
+        prev[1 * ps + idx] = T(m.ux);
+        prev[2 * ps + idx] = T(m.uy);
+        prev[3 * ps + idx] = T(m.uz);
+        prev[4 * ps + idx] = T(m.n);
+    }
 }
 
 // moments + recovery of the current populations: n, e, u_x, u_y, u_z, gamma

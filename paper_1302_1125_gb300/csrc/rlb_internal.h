@@ -19,6 +19,9 @@ struct StepParams {
     double tau_override;     // > 0: fixed tau
     double ghost_f[19], ghost_h[19];   // inlet equilibria
     unsigned *status;        // device status word (bit 0: non-physical cell)
+    // float copies for the FP32-storage kernel (no FP64 conversion on device)
+    float f_k1, f_k2, f_half_lim, f_kw, f_kbulk, f_eta_over_s, f_tau_override;
+    float f_ghost_f[19], f_ghost_h[19];
 };
 
 // launchers (kernel translation units); dim = 1, 2 or 3, euler = 0/1

@@ -1,12 +1,48 @@
-// FP32-storage form of the fused step: populations stored and streamed in
-// float; moment sums, the Landau-frame recovery and the equilibrium
-// coefficients in double.
-#include "rlb_step_impl.cuh"
+// FP32-storage form of the fused step (see rlb_step_f32.cuh): populations
+// stored, streamed and relaxed in float, two cells per thread, double-float
+// moment sums, no FP64 instructions.
+#include "rlb_step_f32.cuh"
 
 namespace rlb {
-cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f,
-                            const float *h, float *fo, float *ho, float *prev, cudaStream_t s)
+
+template <int DIM, bool EULER, bool VEC2>
+static cudaError_t launch_f32(const StepParams &p, const float *f, const float *h, float *fo, float *ho,
+                             float *prev, cudaStream_t s)
 {
-    return launch_step_any<float>(p, dim, euler, f, h, fo, ho, prev, s);
+    const int npairs = (p.nx + 1) / 2;
+    dim3 block, grid;
+    if (DIM == 1) {
+        block = dim3(128, 1, 1);
+        grid = dim3((npairs + 127) / 128, 1, 1);
+    } else {
+        // 32 x 8 threads (64 x 8 cells), two blocks per SM at <= 128 registers:
+        // the best of a sweep over block shapes and register caps on GB300
+        block = dim3(32, 8, 1);
+        grid = dim3((npairs + 31) / 32, (p.ny + 7) / 8, p.nz);
+    }
+    f32::step_f32_kernel<DIM, EULER, VEC2><<<grid, block, 0, s>>>(p, f, h, fo, ho, prev);
+    return cudaGetLastError();
 }
+
+template <bool EULER, bool VEC2>
+static cudaError_t launch_dim(const StepParams &p, int dim, const float *f, const float *h, float *fo,
+                             float *ho, float *prev, cudaStream_t s)
+{
+    if (dim == 1) return launch_f32<1, EULER, VEC2>(p, f, h, fo, ho, prev, s);
+    if (dim == 2) return launch_f32<2, EULER, VEC2>(p, f, h, fo, ho, prev, s);
+    return launch_f32<3, EULER, VEC2>(p, f, h, fo, ho, prev, s);
+}
+
+cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f, const float *h,
+                            float *fo, float *ho, float *prev, cudaStream_t s)
+{
+    // pair loads are 8-byte aligned when every row starts at an even index
+    const bool vec = p.nx % 2 == 0;
+    if (euler)
+        return vec ? launch_dim<true, true>(p, dim, f, h, fo, ho, prev, s)
+                   : launch_dim<true, false>(p, dim, f, h, fo, ho, prev, s);
+    return vec ? launch_dim<false, true>(p, dim, f, h, fo, ho, prev, s)
+               : launch_dim<false, false>(p, dim, f, h, fo, ho, prev, s);
+}
+
 }  // namespace rlb

@@ -1,0 +1,545 @@
+// rlb_step_f32.cuh -- the fused step of the FP32-storage form.
+//
+// One thread updates two x-adjacent cells (x0, x0 + 1) of one (y, z) row.
+// Populations are stored, streamed and relaxed in FP32.  The moment sums
+// T^00 and T^0a are accumulated error-free as double-float pairs (TwoSum),
+// and E^2 - |M|^2, the quantity whose cancellation grows like gamma^2 in the
+// Landau-frame recovery, is formed in double-float before one rounding; the
+// rest of the recovery, tau and the equilibrium coefficients are FP32.  No
+// FP64 instruction is issued.
+//
+// Conservation: the float equilibrium coefficients carry fixed roundings of
+// irrational constants (weights, 4/xi0, 13/9, ...) that would bias their
+// lattice moments identically at every step.  The previous level is kept as
+// the raw moment sums of time t - dt (sum f, sum c_a f, sum h), so the
+// moments 2 f^eq(t) - f^eq(t - dt) must have are known exactly; after the
+// coefficients are formed, their closed-form lattice sums are compared with
+// those targets and the rest coefficient (T^00, N^0) and the axis
+// first-order coefficient (T^0a) absorb the difference, so only unbiased
+// per-cell roundings remain.
+#pragma once
+
+#include <utility>
+
+#include "rlb_device.cuh"
+#include "rlb_internal.h"
+#include "rlb_pair.cuh"
+
+namespace rlb {
+
+namespace f32 {
+
+// constants split into float hi + lo where a double-float value is needed
+constexpr float kXi0SqHi = float(kXi0Sq);
+constexpr float kXi0SqLo = float(kXi0Sq - double(float(kXi0Sq)));
+
+template <int... Is, typename F>
+__device__ __forceinline__ void for_pops(std::integer_sequence<int, Is...>, F &&fn)
+{
+    (fn(std::integral_constant<int, Is>{}), ...);
+}
+#define RLB_F32_POPS std::make_integer_sequence<int, 19>{}
+
+// geometry of one thread's pair of cells
+struct Geo {
+    int idx0, idx1;      // cell indices (idx1 = idx0 when x0 + 1 is outside the grid)
+    int x0;
+    bool has1;
+    int oa, oc;          // offsets of the pairs holding x0-2, x0-1 and x0+2, x0+3
+    unsigned xfix;       // edge columns: clamp or ghost fix-ups (XF_*)
+    int yoff[4], zoff[4];   // offsets of rows/planes at -2, -1, +1, +2 (mapped)
+};
+enum { XF_LO_CLAMP = 1, XF_LO_GHOST = 2, XF_HI_CLAMP = 4, XF_HI_GHOST = 8 };
+
+__device__ __forceinline__ int map1(int c, int n, int lo, int hi, bool &ghost)
+{
+    ghost = false;
+    if (c >= 0 && c < n) return c;
+    const int bc = c < 0 ? lo : hi;
+    if (bc == BC_PERIODIC) {
+        int m = c % n;
+        return m < 0 ? m + n : m;
+    }
+    if (bc == BC_OUTFLOW) return c < 0 ? 0 : n - 1;
+    ghost = true;
+    return c < 0 ? 0 : n - 1;
+}
+
+template <typename P>
+__device__ __forceinline__ f2 ld2(const P *q)
+{
+    const float2 v = __ldg(reinterpret_cast<const float2 *>(q));
+    return f2{v.x, v.y};
+}
+
+// the pair of cells (x0, x0+1) at element offset `off` from idx0
+template <bool VEC2>
+__device__ __forceinline__ f2 ldpair(const float *q, const Geo &g, int off)
+{
+    if constexpr (VEC2) return ld2(q + g.idx0 + off);
+    else return f2{__ldg(q + g.idx0 + off), __ldg(q + g.idx1 + off)};
+}
+
+template <bool VEC2>
+__device__ __forceinline__ void stpair(float *q, const Geo &g, f2 v)
+{
+    if constexpr (VEC2) {
+        *reinterpret_cast<float2 *>(q + g.idx0) = make_float2(v.x, v.y);
+    } else {
+        q[g.idx0] = v.x;
+        if (g.has1) q[g.idx1] = v.y;
+    }
+}
+
+// one value of the x-stencil through the boundary map (odd nx only)
+__device__ __noinline__ float xval_mapped(const float *q, int idx0, int x0, int k, const StepParams &p,
+                                          float ghost)
+{
+    bool gh;
+    const int c = map1(x0 - 2 + k, p.nx, p.bc_lo[0], p.bc_hi[0], gh);
+    return gh ? ghost : __ldg(q + idx0 + (c - x0));
+}
+
+// x0-2 .. x0+3 of one plane.  With even nx every thread loads three aligned
+// pairs; periodic edges wrap to aligned pairs, and the clamped (open) or ghost
+// (inlet) positions of the two edge columns are patched afterwards.
+template <bool VEC2>
+__device__ __forceinline__ void xstencil(const float *q, const Geo &g, const StepParams &p, float ghost,
+                                         float (&v)[6])
+{
+    if constexpr (VEC2) {
+        const f2 a = ld2(q + g.idx0 + g.oa), b = ld2(q + g.idx0), c = ld2(q + g.idx0 + g.oc);
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
+        if (g.xfix) {
+            if (g.xfix & XF_LO_CLAMP) v[1] = v[0];
+            if (g.xfix & XF_LO_GHOST) { v[0] = ghost; v[1] = ghost; }
+            if (g.xfix & XF_HI_CLAMP) { v[4] = v[3]; v[5] = v[3]; }
+            if (g.xfix & XF_HI_GHOST) { v[4] = ghost; v[5] = ghost; }
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 6; ++k) v[k] = xval_mapped(q, g.idx0, g.x0, k, p, ghost);
+    }
+}
+
+// element offset of the row (A = 1) or plane (A = 2) at distance d
+template <int A>
+__device__ __forceinline__ int off_of(const Geo &g, const StepParams &p, int d)
+{
+    const int k = d < 0 ? d + 2 : d + 1;
+    if constexpr (A == 1) return g.yoff[k];
+    else return g.zoff[k];
+}
+
+struct Mac2 {
+    f2 P, ux, uy, uz, n;
+};
+
+// equilibrium coefficients of a pair, weights and diagonal factors folded in
+struct W2 {
+    f2 r0, a0, ab[3], ad[3], d0, db[3], dd[3], dk[3];
+};
+
+// K0, Kb, Kd, Ko of the f equilibrium (see rlb_device.cuh) for a pair
+__device__ __forceinline__ void coef_f2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (&Kd)[3], f2 (&Ko)[3])
+{
+    const f2 u2 = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
+    const f2 g = f2{sqrtf(1.0f + u2.x), sqrtf(1.0f + u2.y)};
+    const f2 A = m.P * bc(13.0f / 9.0f);
+    K0 = A * fma2(bc(-16.0f / 15.0f), u2, bc(1.0f));
+    const f2 b = A * bc(float(kFourOverXi0)) * g;
+    Kb[0] = b * m.ux; Kb[1] = b * m.uy; Kb[2] = b * m.uz;
+    const f2 d = A * bc(52.0f / 15.0f);
+    Kd[0] = d * m.ux * m.ux; Kd[1] = d * m.uy * m.uy; Kd[2] = d * m.uz * m.uz;
+    const f2 o = A * bc(13.0f);
+    Ko[0] = o * m.ux * m.uy; Ko[1] = o * m.ux * m.uz; Ko[2] = o * m.uy * m.uz;
+}
+
+__device__ __forceinline__ void coef_h2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (&Kd)[3], f2 (&Ko)[3])
+{
+    const f2 u2p = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
+    const f2 g = f2{sqrtf(1.0f + u2p.x), sqrtf(1.0f + u2p.y)};
+    const f2 ig = f2{1.0f / g.x, 1.0f / g.y};
+    const f2 ux = m.ux * ig, uy = m.uy * ig, uz = m.uz * ig;
+    const f2 B = m.n * g;
+    const f2 uu = fma2(ux, ux, fma2(uy, uy, uz * uz));
+    K0 = B * fma2(bc(-1.5f), uu, bc(float(kC0Ct)));
+    const f2 b3 = B * bc(3.0f);
+    Kb[0] = b3 * ux; Kb[1] = b3 * uy; Kb[2] = b3 * uz;
+    const f2 b45 = B * bc(4.5f);
+    Kd[0] = b45 * ux * ux; Kd[1] = b45 * uy * uy; Kd[2] = b45 * uz * uz;
+    const f2 b9 = B * bc(9.0f);
+    Ko[0] = b9 * ux * uy; Ko[1] = b9 * ux * uz; Ko[2] = b9 * uy * uz;
+}
+
+// weights folded in (Eqs. 43-45 or 59-60) and the lattice sums set to the
+// exact targets: T0 = sum_i G_i, Ta = sum_i c_ia G_i (only for f).  The rest
+// weight w0 enters only through the target (sum_i w_i = 1).
+__device__ __forceinline__ W2 weigh2(f2 K0, const f2 (&Kb)[3], const f2 (&Kd)[3], const f2 (&Ko)[3],
+                                     float w0, float w1, float w2, f2 T0, const f2 *Ta)
+{
+    (void)w0;
+    W2 e;
+    e.a0 = bc(w1) * K0;
+    e.d0 = bc(w2) * K0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        e.ab[j] = bc(w1) * Kb[j];
+        e.ad[j] = bc(w1) * Kd[j];
+        e.db[j] = bc(2.0f * w2) * Kb[j];
+        e.dd[j] = bc(4.0f * w2) * Kd[j];
+        e.dk[j] = bc(4.0f * w2) * Ko[j];
+    }
+    // sum_i G_i = r0 + 6 a0 + 12 d0 + 2 sum ad + 8 sum dd: the rest coefficient
+    // is the remainder that makes this equal T0, with the other terms summed
+    // error-free (their roundings are correlated, all being K0 times fixed
+    // weights, and a float sum of them is biased); one final rounding
+    df2 R{bc(0.0f), bc(0.0f)};
+    {
+        const f2 p6 = bc(6.0f) * e.a0, p12 = bc(12.0f) * e.d0;
+        acc(R, p6);
+        acc(R, fma2(bc(6.0f), e.a0, -p6));
+        acc(R, p12);
+        acc(R, fma2(bc(12.0f), e.d0, -p12));
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        acc(R, e.ad[j] + e.ad[j]);
+        acc(R, bc(8.0f) * e.dd[j]);
+    }
+    {
+        f2 s, er;
+        two_sum(T0, -R.hi, s, er);
+        e.r0 = s + (er - R.lo);
+    }
+    if (Ta) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            // sum_i c_ia G_i = 2 ab_a + 16 db_a (16 db and the halving are exact)
+            e.ab[j] = bc(0.5f) * (Ta[j] - bc(16.0f) * e.db[j]);
+        }
+    }
+    return e;
+}
+
+template <int I>
+__device__ __forceinline__ f2 eq2(const W2 &e)
+{
+    constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+    constexpr int sh = shell<I>();
+    if constexpr (sh == 0) {
+        return e.r0;
+    } else if constexpr (sh == 1) {
+        constexpr int a = cx != 0 ? 0 : (cy != 0 ? 1 : 2);
+        constexpr int s = cx + cy + cz;
+        const f2 base = e.a0 + e.ad[a];
+        return s > 0 ? base + e.ab[a] : base - e.ab[a];
+    } else {
+        constexpr int a = cx != 0 ? 0 : 1;
+        constexpr int b = cz != 0 ? 2 : 1;
+        constexpr int ca = a == 0 ? cx : cy, cb = b == 2 ? cz : cy;
+        constexpr int ko = (a == 0 && b == 1) ? 0 : ((a == 0 && b == 2) ? 1 : 2);
+        f2 v = e.d0 + (e.dd[a] + e.dd[b]);
+        v = ca > 0 ? v + e.db[a] : v - e.db[a];
+        v = cb > 0 ? v + e.db[b] : v - e.db[b];
+        v = ca * cb > 0 ? v + e.dk[ko] : v - e.dk[ko];
+        return v;
+    }
+}
+
+// Landau-frame recovery of a pair from the raw sums S = sum f, V_a = sum c_a f
+// (double-float) and Sh = sum h: E = xi0^2 S, M = xi0 V,
+// E^2 - |M|^2 = xi0^2 (xi0^2 S^2 - |V|^2) formed in double-float,
+// P = (E^2 - |M|^2) / (E + sqrt(E^2 + 3 (E^2 - |M|^2))), gamma^2 = (E + P)/(4 P),
+// u' = M / (4 P gamma), n = N^0 / gamma
+__device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 &Vy, const df2 &Vz,
+                                         f2 Sh, bool &ok0, bool &ok1)
+{
+    const df2 V2 = dadd(dadd(sq(Vx), sq(Vy)), sq(Vz));
+    const df2 Dr = dadd(dscale(sq(S), kXi0SqHi, kXi0SqLo), dneg(V2));
+    const f2 D = bc(float(kXi0Sq)) * (Dr.hi + Dr.lo);
+    const f2 E = bc(float(kXi0Sq)) * (S.hi + S.lo);
+    const f2 root2 = fma2(E, E, bc(3.0f) * D);
+    const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
+    Mac2 m;
+    m.P = f2{D.x / den.x, D.y / den.y};
+    const f2 fourP = bc(4.0f) * m.P;
+    const f2 g2 = f2{(E.x + m.P.x) / fourP.x, (E.y + m.P.y) / fourP.y};
+    const f2 g = f2{sqrtf(g2.x), sqrtf(g2.y)};
+    const f2 s = f2{float(kXi0) / (fourP.x * g.x), float(kXi0) / (fourP.y * g.y)};
+    m.ux = (Vx.hi + Vx.lo) * s;
+    m.uy = (Vy.hi + Vy.lo) * s;
+    m.uz = (Vz.hi + Vz.lo) * s;
+    m.n = f2{float(kXi0) * Sh.x / g.x, float(kXi0) * Sh.y / g.y};
+    ok0 = E.x > 0.0f && D.x > 0.0f && isfinite(m.n.x) && isfinite(s.x);
+    ok1 = E.y > 0.0f && D.y > 0.0f && isfinite(m.n.y) && isfinite(s.y);
+    return m;
+}
+
+// the same recovery from plain float sums (used for the previous level, whose
+// equilibrium only shapes the non-conserved part of 2 f^eq(t) - f^eq(t - dt))
+__device__ __forceinline__ Mac2 recover2f(f2 S, f2 Vx, f2 Vy, f2 Vz, f2 Sh)
+{
+    const f2 E = bc(float(kXi0Sq)) * S;
+    const f2 M2 = bc(float(kXi0Sq)) * fma2(Vx, Vx, fma2(Vy, Vy, Vz * Vz));
+    const f2 D = fma2(E, E, -M2);
+    const f2 root2 = fma2(E, E, bc(3.0f) * D);
+    const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
+    Mac2 m;
+    m.P = f2{D.x / den.x, D.y / den.y};
+    const f2 fourP = bc(4.0f) * m.P;
+    const f2 g = f2{sqrtf((E.x + m.P.x) / fourP.x), sqrtf((E.y + m.P.y) / fourP.y)};
+    const f2 s = f2{float(kXi0) / (fourP.x * g.x), float(kXi0) / (fourP.y * g.y)};
+    m.ux = Vx * s;
+    m.uy = Vy * s;
+    m.uz = Vz * s;
+    m.n = f2{float(kXi0) * Sh.x / g.x, float(kXi0) * Sh.y / g.y};
+    return m;
+}
+
+// tau from eta/s (Eq. 41 with the entropy of Sec. III), float
+__device__ __forceinline__ float tau1(float P, float n, float eta_over_s)
+{
+    const float T = P / n;
+    const float lam = n * float(kPi2Over16) / (T * T * T);
+    const float sfac = fmaxf(4.0f - logf(lam), float(kSMin));
+    return 0.5f + 13.0f * eta_over_s * sfac / (4.0f * T);
+}
+
+// streaming increment of population I along axis A for the pair (+ bulk lap)
+template <bool IS_F, int I, int A, bool VEC2>
+__device__ __forceinline__ void axis2(const float *q, const Geo &g, const StepParams &p, const float (&xv)[6],
+                                      f2 C, float k1, float k2, float hl, f2 &inc, f2 &lap)
+{
+    constexpr int c = cdir<I, A>();
+    constexpr bool need_lap = IS_F && I != 0;
+    const float k = (c == 1 || c == -1) ? k1 : k2;
+    if constexpr (A == 0) {
+        if constexpr (c > 0) {
+            const float dm3 = xv[1] - xv[0], dm1 = xv[2] - xv[1], dp1 = xv[3] - xv[2], dp3 = xv[4] - xv[3];
+            const float mA = mm(dp1, dm1), mB = mm(dm1, dm3), mC = mm(dp3, dp1);
+            const f2 D = fma2(bc(hl), mk(mA, mC) - mk(mB, mA), mk(dm1, dp1));
+            inc = fma2(bc(-k), D, inc);
+            if constexpr (need_lap) lap = lap + (mk(dp1, dp3) - mk(dm1, dp1));
+        } else if constexpr (c < 0) {
+            const float dm1 = xv[2] - xv[1], dp1 = xv[3] - xv[2], dp3 = xv[4] - xv[3], dp5 = xv[5] - xv[4];
+            const float m1 = mm(dm1, dp1), m2 = mm(dp1, dp3), m3 = mm(dp3, dp5);
+            const f2 D = fma2(bc(-hl), mk(m2, m3) - mk(m1, m2), mk(dp1, dp3));
+            inc = fma2(bc(k), D, inc);
+            if constexpr (need_lap) lap = lap + (mk(dp1, dp3) - mk(dm1, dp1));
+        } else if constexpr (need_lap) {
+            const float dm1 = xv[2] - xv[1], dp1 = xv[3] - xv[2], dp3 = xv[4] - xv[3];
+            lap = lap + (mk(dp1, dp3) - mk(dm1, dp1));
+        }
+    } else {
+        if constexpr (c > 0) {
+            const f2 Aq = ldpair<VEC2>(q, g, off_of<A>(g, p, -2)), B = ldpair<VEC2>(q, g, off_of<A>(g, p, -1));
+            const f2 Dq = ldpair<VEC2>(q, g, off_of<A>(g, p, 1));
+            const f2 d0 = B - Aq, d1 = C - B, d2 = Dq - C;
+            const f2 Dv = fma2(bc(hl), mm(d2, d1) - mm(d1, d0), d1);
+            inc = fma2(bc(-k), Dv, inc);
+            if constexpr (need_lap) lap = lap + (d2 - d1);
+        } else if constexpr (c < 0) {
+            const f2 B = ldpair<VEC2>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2>(q, g, off_of<A>(g, p, 1));
+            const f2 Eq = ldpair<VEC2>(q, g, off_of<A>(g, p, 2));
+            const f2 e0 = C - B, e1 = Dq - C, e2 = Eq - Dq;
+            const f2 Dv = fma2(bc(-hl), mm(e1, e2) - mm(e0, e1), e1);
+            inc = fma2(bc(k), Dv, inc);
+            if constexpr (need_lap) lap = lap + (e1 - e0);
+        } else if constexpr (need_lap) {
+            const f2 B = ldpair<VEC2>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2>(q, g, off_of<A>(g, p, 1));
+            lap = lap + ((Dq - C) - (C - B));
+        }
+    }
+}
+
+// f (or h) + streaming (+ bulk) of population I for the pair: the explicit part of Eq. 57
+template <int DIM, bool IS_F, int I, bool VEC2>
+__device__ __forceinline__ f2 streamed2(const float *q, const Geo &g, const StepParams &p, float ghost,
+                                        float k1, float k2, float hl, float kb)
+{
+    constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
+    float xv[6];
+    f2 C;
+    if constexpr (xneed) {
+        xstencil<VEC2>(q, g, p, ghost, xv);
+        C = mk(xv[2], xv[3]);
+    } else {
+        C = ldpair<VEC2>(q, g, 0);
+    }
+    f2 inc = bc(0.0f), lap = bc(0.0f);
+    if constexpr (xneed) axis2<IS_F, I, 0, VEC2>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 1) axis2<IS_F, I, 1, VEC2>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 2) axis2<IS_F, I, 2, VEC2>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (IS_F && I != 0) inc = fma2(bc(kb), lap, inc);
+    return C + inc;
+}
+
+template <int DIM, bool EULER, bool VEC2>
+__global__ void __launch_bounds__(256, VEC2 ? 2 : 1) step_f32_kernel(const StepParams p, const float *__restrict__ f,
+                                                       const float *__restrict__ h, float *__restrict__ fo,
+                                                       float *__restrict__ ho, float *__restrict__ prev)
+{
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x0 >= p.nx || y >= p.ny) return;
+    const long long ps = p.ps;
+
+    Geo g;
+    g.idx0 = x0 + p.nx * (y + p.ny * z);
+    g.x0 = x0;
+    g.has1 = x0 + 1 < p.nx;
+    g.idx1 = g.has1 ? g.idx0 + 1 : g.idx0;
+    g.oa = -2;
+    g.oc = 2;
+    g.xfix = 0u;
+    if (VEC2) {
+        if (x0 == 0) {   // x0-2, x0-1 are outside
+            if (p.bc_lo[0] == BC_PERIODIC) g.oa = p.nx - 2;
+            else { g.oa = 0; g.xfix |= p.bc_lo[0] == BC_OUTFLOW ? XF_LO_CLAMP : XF_LO_GHOST; }
+        }
+        if (x0 + 2 >= p.nx) {   // x0+2, x0+3 are outside
+            if (p.bc_hi[0] == BC_PERIODIC) g.oc = -x0;
+            else { g.oc = 0; g.xfix |= p.bc_hi[0] == BC_OUTFLOW ? XF_HI_CLAMP : XF_HI_GHOST; }
+        }
+    }
+    {
+        const int ds[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            bool gh;
+            g.yoff[k] = DIM > 1 ? (map1(y + ds[k], p.ny, p.bc_lo[1], p.bc_hi[1], gh) - y) * p.nx : 0;
+            g.zoff[k] = DIM > 2 ? (map1(z + ds[k], p.nz, p.bc_lo[2], p.bc_hi[2], gh) - z) * p.nx * p.ny : 0;
+        }
+    }
+    const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim, kb = p.f_kbulk;
+    const float eos = p.f_eta_over_s;
+
+    if constexpr (!EULER) {
+        // raw sums of the local populations: S = sum f, V_a = sum c_a f
+        // (double-float), Sh = sum h
+        df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
+        for_pops(RLB_F32_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const f2 v = ldpair<VEC2>(f + I * ps, g, 0);
+            acc(S, v);
+            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
+            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
+            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
+            acc(Hs, ldpair<VEC2>(h + I * ps, g, 0));
+        });
+        const f2 Sh = Hs.hi + Hs.lo;
+        bool ok0, ok1;
+        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
+
+        f2 kap;
+        {
+            float t0, t1;
+            if (p.f_tau_override > 0.0f) {
+                t0 = t1 = p.f_tau_override;
+            } else {
+                t0 = tau1(mt.P.x, mt.n.x, eos);
+                t1 = tau1(mt.P.y, mt.n.y, eos);
+            }
+            const float kw = p.f_kw;
+            const float w0 = kw / t0, w1 = kw / t1;
+            kap = f2{w0 / (1.0f + w0), w1 / (1.0f + w1)};
+        }
+
+        // the previous level holds the raw moment sums of time t - dt, so the
+        // targets of 2 f^eq(t) - f^eq(t - dt) are exact: T = 2 S(t) - S(t - dt)
+        const f2 Sp = ldpair<VEC2>(prev + 0 * ps, g, 0);
+        const f2 Vpx = ldpair<VEC2>(prev + 1 * ps, g, 0);
+        const f2 Vpy = ldpair<VEC2>(prev + 2 * ps, g, 0);
+        const f2 Vpz = ldpair<VEC2>(prev + 3 * ps, g, 0);
+        const f2 Shp = ldpair<VEC2>(prev + 4 * ps, g, 0);
+        const Mac2 mp = recover2f(Sp, Vpx, Vpy, Vpz, Shp);
+        const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
+        f2 Ta[3];
+        Ta[0] = fma2(bc(2.0f), Vx.hi + Vx.lo, -Vpx);
+        Ta[1] = fma2(bc(2.0f), Vy.hi + Vy.lo, -Vpy);
+        Ta[2] = fma2(bc(2.0f), Vz.hi + Vz.lo, -Vpz);
+
+        {
+            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
+            coef_f2(mt, K0, Kb, Kd, Ko);
+            coef_f2(mp, L0, Lb, Ld, Lo);
+            K0 = fma2(bc(2.0f), K0, -L0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
+                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
+                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
+            }
+            const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), T0, Ta);
+            for_pops(RLB_F32_POPS, [&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                const f2 pre = streamed2<DIM, true, I, VEC2>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
+                stpair<VEC2>(fo + I * ps, g, fma2(kap, eq2<I>(ef) - pre, pre));
+            });
+        }
+        {
+            const f2 T0h = fma2(bc(2.0f), Sh, -Shp);
+            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
+            coef_h2(mt, K0, Kb, Kd, Ko);
+            coef_h2(mp, L0, Lb, Ld, Lo);
+            K0 = fma2(bc(2.0f), K0, -L0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
+                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
+                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
+            }
+            const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
+            for_pops(RLB_F32_POPS, [&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                const f2 pre = streamed2<DIM, false, I, VEC2>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb);
+                stpair<VEC2>(ho + I * ps, g, fma2(kap, eq2<I>(eh) - pre, pre));
+            });
+        }
+        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
+        stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
+        stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
+        stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
+        stpair<VEC2>(prev + 4 * ps, g, Sh);
+    } else {
+        // Euler mode (Sec. III): f, h <- equilibria of the streamed state
+        df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
+        for_pops(RLB_F32_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const f2 v = streamed2<DIM, true, I, VEC2>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
+            acc(S, v);
+            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
+            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
+            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
+            acc(Hs, streamed2<DIM, false, I, VEC2>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb));
+        });
+        const f2 Sh = Hs.hi + Hs.lo;
+        bool ok0, ok1;
+        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
+        const f2 Ta[3] = {Vx.hi + Vx.lo, Vy.hi + Vy.lo, Vz.hi + Vz.lo};
+        f2 K0, Kb[3], Kd[3], Ko[3];
+        coef_f2(mt, K0, Kb, Kd, Ko);
+        const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), S.hi + S.lo, Ta);
+        coef_h2(mt, K0, Kb, Kd, Ko);
+        const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), Sh, nullptr);
+        for_pops(RLB_F32_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            stpair<VEC2>(fo + I * ps, g, eq2<I>(ef));
+            stpair<VEC2>(ho + I * ps, g, eq2<I>(eh));
+        });
+        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
+        stpair<VEC2>(prev + 1 * ps, g, Ta[0]);
+        stpair<VEC2>(prev + 2 * ps, g, Ta[1]);
+        stpair<VEC2>(prev + 3 * ps, g, Ta[2]);
+        stpair<VEC2>(prev + 4 * ps, g, Sh);
+    }
+}
+
+}  // namespace f32
+}  // namespace rlb

@@ -183,28 +183,45 @@ def test_totals_match_oracle(orc):
 
 
 def test_full_size_cloud_3d_sampled_cells(orc):
-    # the benchmark's workload and launch configuration, full size
+    # the benchmark's workload and launch configuration, full size (FP32 form)
     w = W.cloud_3d()
     g = rlb.Grid.from_workload(w)
     g.init(*[torch.as_tensor(a, device="cuda") for a in w.fields()])
-    g.step(3)
-    f0, h0, p0 = g.get_state()
+    g.step(2)
+    fa, ha, _ = g.get_state()          # time level 2
     g.step(1)
-    f1, h1, p1 = g.get_state()
+    f0, h0, p0 = g.get_state()         # time level 3; p0 = raw moment sums of level 2
+    g.step(1)
+    f1, h1, p1 = g.get_state()         # time level 4; p1 = raw moment sums of level 3
     rng = np.random.default_rng(2024)
     nx, ny, nz = w.nx, w.ny, w.nz
     special = [x + nx * (y + ny * z) for x in (0, 1, 2, 63, 64, nx - 2, nx - 1)
                for y in (0, ny // 2, ny - 1) for z in (0, nz // 2, nz - 1)]
     cells = np.unique(np.r_[rng.integers(0, w.N, 3000), special]).astype(np.int64)
-    fo, ho, mo, bad = orc.step_cells(oparams(orc, w), f0, h0, p0, cells)
+    # the oracle's previous level: its own moments and recovery of level 2
+    prev = np.zeros((5, w.N), np.float32)
+    for c in cells:
+        mac, bad = orc.recover(orc.moments(fa[:, c].astype(np.float64), ha[:, c].astype(np.float64)))
+        assert not bad
+        prev[:, c] = mac
+    fo, ho, mo, bad = orc.step_cells(oparams(orc, w), f0, h0, prev, cells)
     assert bad == 0
+    # one FP32 step rounds each population about 50 times (streaming, moments,
+    # recovery, coefficients, relaxation) on values up to ~3x the population's
+    # scale; 64 units of float rounding (2^-24 each) of the plane's scale bound it
+    tol = 64 * 2.0 ** -24
     for a, b in ((f1[:, cells], fo.T), (h1[:, cells], ho.T)):
         for k in range(19):
             err = np.abs(a[k] - b[k]).max() / np.abs(b[k]).max()
-            assert err <= 2e-6, (k, err)
+            assert err <= tol, (k, err)
+    # the stored previous level is the raw sums of the step's own input
+    # (c_a = 1, so the oracle's lattice vectors are the integer vectors c_i)
+    _, c, _, _, _ = orc.lattice()
+    f0c = f0[:, cells].astype(np.float64)
+    sums = np.vstack([f0c.sum(0), c.T @ f0c, h0[:, cells].astype(np.float64).sum(0)])
     for k in range(5):
-        scale = np.abs(mo[:, k]).max() if k in (0, 4) else np.abs(mo[:, 1:4]).max() + 1e-300
-        assert np.abs(p1[k, cells] - mo[:, k]).max() / scale <= 1e-6, k
+        scale = np.abs(sums[k]).max() if k in (0, 4) else np.abs(sums[1:4]).max() + 1e-300
+        assert np.abs(p1[k, cells] - sums[k]).max() / scale <= 1e-6, k
 
 
 def test_checkpoint_resume_is_bit_exact():
