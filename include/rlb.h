@@ -205,6 +205,134 @@ RLB_API rlb_status rlb_conserved_totals_noalloc(const void *f, const void *h, in
                                                 long long plane_stride, int precision,
                                                 double *out_device, void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Batched tubes.
+ *
+ * B independent one-dimensional tubes (grid nx_b x 1 x 1 each, zero-gradient
+ * outflow at both ends: the paper's open ends, Sec. III), each with its own
+ * length, eta/s and zeta/s, advanced by the step of Eq. 57 in the
+ * FP32-storage form (the same per-cell arithmetic as rlb_step with
+ * RLB_FP32_STORAGE).  One persistent kernel runs every tube for its own
+ * number of steps; a CUDA graph replays that launch.
+ *
+ * Work division: tubes are grouped into jobs (one tube, or up to 32
+ * consecutive tubes of similar length and step count) and each job is run,
+ * all of its steps, by one cluster of `cluster` thread blocks that meet at
+ * the hardware cluster barrier (the block barrier for cluster = 1) after
+ * every step.  Jobs are assigned to the clusters that fit on the GPU at once,
+ * longest first, each to the least loaded cluster (rlb_batch_plan).
+ *
+ * Packed layout of every field passed through this part of the ABI: tube b
+ * holds cells [o_b, o_b + nx_b) with o_0 = 0, o_{b+1} = o_b + nx_b; total =
+ * o_B cells.  Ownership, streams and errors as above; rlb_batch_last_error
+ * gives the text of the last error of a batch (of the thread for NULL).
+ * ------------------------------------------------------------------------ */
+typedef struct rlb_batch rlb_batch;
+
+/* Launch shape of the persistent tube kernel. */
+typedef struct {
+    int threads;           /* threads per block: a multiple of 32, <= bound */
+    int bound;             /* kernel variant by launch bound: 512 (128 registers per thread),
+                            * 384 (168) or 256 (unconstrained) threads */
+    int cluster;           /* blocks per cluster sharing one job: 1, 2, 4 or 8 */
+    int pairs_per_thread;  /* job capacity: consecutive tubes are grouped while their cell pairs
+                            * fit in cluster x threads x pairs_per_thread (a longer tube is a job
+                            * of its own); each thread updates two adjacent cells per pass */
+    double ms;             /* rlb_batch_autotune: measured time of the trial in ms, -1 = did not run */
+} rlb_batch_tuning;
+
+/* Create a batch of B tubes (1 <= B <= 65535): nx[b] >= 1 cells,
+ * eta_over_s[b] and zeta_over_s[b] >= 0 (tau through Eq. 41 and alpha
+ * through Eq. 56 per tube, as in rlb_create; opts->alpha_override >= 0 sets
+ * one alpha for all tubes).  opts may be NULL: defaults of
+ * rlb_default_options with precision RLB_FP32_STORAGE.  Requirements:
+ * precision RLB_FP32_STORAGE, euler_mode 0, at most 2^30 stored cells
+ * (each tube stored from a 128-byte boundary).  RLB_E_UNSTABLE if
+ * 2 (c_0/c_t) dt/dx > 1 or 2 (c_0 nu / c_t) dt alpha_b > 1 for a tube.
+ * Allocates 81 population and previous-level planes over the stored cells
+ * plus staging and tables (about 324 B per cell + 48 B per cell of
+ * staging).  *out receives the handle (NULL on failure; message in
+ * rlb_batch_last_error(NULL)). */
+RLB_API rlb_status rlb_batch_create(int B, const int *nx, const double *eta_over_s,
+                                    const double *zeta_over_s, int limiter, const rlb_options *opts,
+                                    rlb_batch **out);
+
+/* Initialise every tube to equilibrium (as rlb_init): n, T, ux are packed
+ * arrays of `total` doubles (three-velocity along the tube, |u| < 1).
+ * RLB_E_INVALID if a cell has n <= 0, T <= 0 or |u| >= 1.  Synchronous. */
+RLB_API rlb_status rlb_batch_init(rlb_batch *b, const double *n, const double *T, const double *ux,
+                                  int on_device);
+
+/* Advance tube b by nsteps[b] steps of Eq. 57 (host array of B counts in
+ * [0, 2^31 - 1]; 0 leaves a tube unchanged) in one launch of the persistent
+ * kernel, replayed from a CUDA graph.  The job plan is rebuilt when the step
+ * counts or the tuning change.  Waits for the launch and returns
+ * RLB_E_NONPHYSICAL if any cell of any step was non-physical. */
+RLB_API rlb_status rlb_batch_step(rlb_batch *b, const long long *nsteps);
+
+/* Macroscopic fields of every tube (as rlb_macroscopic): out holds 6 x total
+ * doubles, planes n, e, u_x, u_y, u_z, gamma, each packed.  Synchronous. */
+RLB_API rlb_status rlb_batch_macroscopic(rlb_batch *b, double *out, int on_device);
+
+/* Per-tube totals of T^00, T^0x, T^0y, T^0z and N^0 (Eq. 36 summed over the
+ * tube's cells, FP64, deterministic order): out[5 b + k], 5 B host doubles.
+ * Synchronous. */
+RLB_API rlb_status rlb_batch_totals(rlb_batch *b, double *out);
+
+/* The job plan of a launch, computed on the host without a GPU (the plan
+ * rlb_batch_step uploads).  Tubes with nsteps > 0 are ordered by step count,
+ * then length, both descending (ties by index); consecutive tubes are
+ * grouped into jobs while a job has fewer than 32 tubes and its cell pairs
+ * (ceil(nx / 2) per tube) fit in t->cluster x t->threads x
+ * t->pairs_per_thread; a job's cost is its largest step count x
+ * ceil(pairs / (cluster x threads)) passes; jobs are taken in decreasing
+ * cost and each is given to the cluster with the least cost so far (lowest
+ * index on ties).  Outputs: order[B] (tube ids; tubes with no steps last),
+ * jobs[4 x njobs] as (first position in order, tube count, steps, pairs),
+ * grouped by cluster with cluster c owning jobs cl_start[c] ..
+ * cl_start[c + 1] - 1 (cl_start has nclusters + 1 entries), *critical = the
+ * largest per-cluster cost (NULL to skip).  jobs must hold 4 B ints.
+ * RLB_E_INVALID for bad arguments (message in rlb_batch_last_error(NULL)). */
+RLB_API rlb_status rlb_batch_plan(int B, const int *nx, const long long *nsteps,
+                                  const rlb_batch_tuning *t, int nclusters, int *order, int *jobs,
+                                  int *njobs, int *cl_start, long long *critical);
+
+/* Autotuner: time the launch shapes on this batch and keep the fastest.
+ * Each trial restores the state, runs ceil(nsteps[b] / divisor) steps per
+ * tube in one launch and is timed with CUDA events; the candidates are every
+ * (bound, threads <= bound) of {512, 384, 256} x {128, 256, 384, 512} with
+ * clusters 1, 2, 4, 8 and pairs_per_thread 1, then pairs_per_thread 2 and 4
+ * for the best of those.  The state is restored at the end (the tuning run
+ * does not advance the batch).  trials (max_trials entries, may be NULL
+ * when max_trials = 0) receives the trials in order with their times,
+ * *n_trials their number; *best the one kept.  Needs a temporary device
+ * buffer the size of the state (RLB_E_NOMEM if it cannot be had). */
+RLB_API rlb_status rlb_batch_autotune(rlb_batch *b, const long long *nsteps, int divisor,
+                                      rlb_batch_tuning *trials, int max_trials, int *n_trials,
+                                      rlb_batch_tuning *best);
+
+/* Set or read the launch shape (RLB_E_INVALID if it is malformed or does not
+ * fit on the device).  *resident_clusters (may be NULL) receives how many
+ * clusters of that shape the device holds at once: the persistent grid. */
+RLB_API rlb_status rlb_batch_set_tuning(rlb_batch *b, const rlb_batch_tuning *t);
+RLB_API rlb_status rlb_batch_get_tuning(const rlb_batch *b, rlb_batch_tuning *t,
+                                        int *resident_clusters);
+
+/* Change the stream later calls use (cudaStream_t, NULL = legacy default). */
+RLB_API rlb_status rlb_batch_set_stream(rlb_batch *b, void *cuda_stream);
+
+/* total = sum of nx_b (0 for NULL). */
+RLB_API long long rlb_batch_total_cells(const rlb_batch *b);
+
+/* Kernels this batch has launched (a graph replay counts as one). */
+RLB_API long long rlb_batch_launch_count(const rlb_batch *b);
+
+/* Release the batch's device and pinned memory.  NULL is a no-op. */
+RLB_API void rlb_batch_destroy(rlb_batch *b);
+
+/* Text of the last error of b (of the calling thread for NULL).  Never NULL. */
+RLB_API const char *rlb_batch_last_error(const rlb_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librlb.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["rlb_api.cu", "rlb_aux.cu", "rlb_step_f64.cu", "rlb_step_f32.cu", "rlb_noalloc.cu"]
+SOURCES = ["rlb_api.cu", "rlb_aux.cu", "rlb_step_f64.cu", "rlb_step_f32.cu", "rlb_noalloc.cu",
+           "rlb_batch_api.cpp", "rlb_batch_aux.cu", "rlb_batch_ca.cu", "rlb_batch_cg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++20", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "--expt-relaxed-constexpr"]
@@ -43,7 +44,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(BUILD, os.path.splitext(src)[0] + ".o")
         cmd = [cc, *ARCH, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")

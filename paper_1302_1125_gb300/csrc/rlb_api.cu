@@ -71,7 +71,7 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 double alpha_from(double zeta_over_s, const rlb_options &o)
 {
     if (o.alpha_override >= 0.0) return o.alpha_override;
-    return 27.0 * zeta_over_s * 4.0 / (4.0 * 2197.0);   // nu^6 = 13^3
+    return rlb::alpha_of_zeta(zeta_over_s);
 }
 
 int active_axes(const rlb_grid &g)

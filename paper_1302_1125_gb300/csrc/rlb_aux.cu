@@ -1,9 +1,8 @@
 // Initialisation, macroscopic output and conserved-total kernels.
-#include "rlb_kernels.cuh"
+#include "rlb_cellops.cuh"
 
 namespace rlb {
 
-// f = f^eq(P = nT, u), h = h^eq(n, u), previous level = this state
 template <typename T>
 __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
                             const double *__restrict__ Tt, const double *__restrict__ ux,
@@ -13,48 +12,7 @@ __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N) return;
-    const double vx = ux[idx], vy = uy[idx], vz = uz[idx];
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double g = 1.0 / sqrt(1.0 - v2);
-    if (!(n[idx] > 0.0 && Tt[idx] > 0.0 && v2 < 1.0 && isfinite(n[idx] * Tt[idx]) && isfinite(g)))
-        atomicOr(status, unsigned(ST_NONPHYSICAL));
-    Macro m;
-    m.P = n[idx] * Tt[idx];
-    m.ux = g * vx;
-    m.uy = g * vy;
-    m.uz = g * vz;
-    m.n = n[idx];
-    Coef<double> a;
-    coef_f(m, a);
-    const EqW<T> kf = weigh_f<T>(a);
-    coef_h(m, a);
-    const EqW<T> kh = weigh_h<T>(a);
-    double S = 0.0, Vx = 0.0, Vy = 0.0, Vz = 0.0, Sh = 0.0;
-    for_pops(RLB_POPS, [&](auto ic) {
-        constexpr int I = decltype(ic)::value;
-        const T fv = eq_pop<I>(kf), hv = eq_pop<I>(kh);
-        f[I * ps + idx] = fv;
-        h[I * ps + idx] = hv;
-        S += double(fv);
-        Sh += double(hv);
-        if constexpr (cdir<I, 0>() != 0) Vx += double(cdir<I, 0>()) * double(fv);
-        if constexpr (cdir<I, 1>() != 0) Vy += double(cdir<I, 1>()) * double(fv);
-        if constexpr (cdir<I, 2>() != 0) Vz += double(cdir<I, 2>()) * double(fv);
-    });
-    if constexpr (sizeof(T) == 4) {
-        // FP32-storage form: the previous level is the raw moment sums
-        prev[0 * ps + idx] = T(S);
-        prev[1 * ps + idx] = T(Vx);
-        prev[2 * ps + idx] = T(Vy);
-        prev[3 * ps + idx] = T(Vz);
-        prev[4 * ps + idx] = T(Sh);
-    } else {
-        prev[0 * ps + idx] = T(m.P);
-        prev[1 * ps + idx] = T(m.ux);
-        prev[2 * ps + idx] = T(m.uy);
-        prev[3 * ps + idx] = T(m.uz);
-        prev[4 * ps + idx] = T(m.n);
-    }
+    init_cell<T>(idx, idx, ps, n, Tt, ux, uy, uz, f, h, prev, status);
 }
 
 // moments + recovery of the current populations: n, e, u_x, u_y, u_z, gamma
@@ -65,26 +23,7 @@ __global__ void macro_kernel(int N, long long ps, const T *__restrict__ f,
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N) return;
-    double sf = 0.0, sh = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
-    for_pops(RLB_POPS, [&](auto ic) {
-        constexpr int I = decltype(ic)::value;
-        const double fv = double(f[I * ps + idx]);
-        sf += fv;
-        sh += double(h[I * ps + idx]);
-        if constexpr (cdir<I, 0>() != 0) mx += double(cdir<I, 0>()) * fv;
-        if constexpr (cdir<I, 1>() != 0) my += double(cdir<I, 1>()) * fv;
-        if constexpr (cdir<I, 2>() != 0) mz += double(cdir<I, 2>()) * fv;
-    });
-    Macro m;
-    if (!recover(kXi0Sq * sf, kXi0 * mx, kXi0 * my, kXi0 * mz, kXi0 * sh, m))
-        atomicOr(status, unsigned(ST_NONPHYSICAL));
-    const double g = sqrt(1.0 + m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
-    out[0 * (long long)N + idx] = m.n;
-    out[1 * (long long)N + idx] = 3.0 * m.P;
-    out[2 * (long long)N + idx] = m.ux / g;
-    out[3 * (long long)N + idx] = m.uy / g;
-    out[4 * (long long)N + idx] = m.uz / g;
-    out[5 * (long long)N + idx] = g;
+    macro_cell<T>(idx, ps, f, h, out, idx, N, status);
 }
 
 // per-block partial sums of (T^00, T^0x, T^0y, T^0z, N^0); fixed grid and

@@ -10,22 +10,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "rlb_consts.h"
+
 namespace rlb {
-
-// ---------------------------------------------------------------------------
-// Lattice constants (Sec. II.A, Eqs. 42-46 and 59-60), nu = sqrt(13)
-// ---------------------------------------------------------------------------
-constexpr double kXi0 = 1.44115338424578420134928;      // c_t/c_0 = sqrt(27)/nu
-constexpr double kXi0Sq = 27.0 / 13.0;
-constexpr double kC0Ct = 0.693888666488710911760766;    // c_0/c_t
-constexpr double kOmegaC = 2.50185116648837831287298;   // (c_0/c_t) nu = 13/sqrt(27)
-constexpr double kFourOverXi0 = 2.77555466595484364704306;
-constexpr double kPi2Over16 = 0.616850275068084913677156;  // 1 / (d_G / pi^2), d_G = 16
-constexpr double kSMin = 1e-3;  // floor of 4 - ln(lambda) in the entropy density
-
-// weights of f (Eqs. 43-45; independent of nu) and of h (Eqs. 59-60, c_a = 1)
-constexpr double kW0 = -539.0 / 676.0, kW1 = 99.0 / 338.0, kW2 = 9.0 / 2704.0;
-constexpr double kWh0 = 0.1, kWh1 = 6.0 / 35.0 - 1.0 / 42.0, kWh2 = 1.0 / 84.0 - 3.0 / 280.0;
 
 // integer velocity components c_i (c_a = 1; the diagonals carry 2 c_a)
 struct Dir {

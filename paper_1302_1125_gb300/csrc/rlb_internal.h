@@ -43,4 +43,66 @@ cudaError_t launch_totals(int fp32, int N, long long ps, const void *f, const vo
 // set the text rlb_last_error(NULL) returns on this thread
 void set_thread_error(const char *msg);
 
+// ---------------------------------------------------------------------------
+// Batched tubes (rlb_batch.cuh): tables the host builds for the persistent
+// launch.
+// ---------------------------------------------------------------------------
+namespace batch {
+
+constexpr int kMaxJobTubes = 32;   // tubes per job
+constexpr int kAlignCells = 32;    // tube storage offsets are multiples of this (128 B)
+
+struct Tube {
+    int off;     // storage offset of cell 0 in every plane (multiple of kAlignCells)
+    int nx;      // cells
+    float eos;   // eta/s
+    float kb;    // bulk prefactor (c0/ct) nu dt alpha (Eq. 57)
+};
+
+struct Job {
+    int first;   // position in the tube order of the job's first tube
+    int count;   // tubes in the job (1 .. kMaxJobTubes)
+    int steps;   // steps the job runs: the largest step count of its tubes
+    int pairs;   // sum over its tubes of ceil(nx / 2)
+};
+
+struct Args {
+    StepParams p;           // constants shared by all tubes, status word
+    const Tube *tubes;      // [B]
+    const int *order;       // [B] tube ids, the order jobs refer to
+    const int *steps;       // [B] steps of each tube in this launch
+    int *par;               // [B] buffer (0 or 1) holding each tube's current level
+    const Job *jobs;        // jobs of cluster c: [cl_start[c], cl_start[c + 1])
+    const int *cl_start;    // [nclusters + 1]
+    int nclusters;
+    int cluster;            // blocks per cluster
+    float *f0, *h0, *f1, *h1, *prev;
+    long long ps;
+};
+
+// launch the persistent tube kernel (grid = a.nclusters x cluster blocks of
+// `threads`), or, when nclusters_out is non-NULL, store the number of clusters
+// that fit on the device at once instead of launching.  bound = the kernel
+// variant's launch bound (256, 384 or 512 threads; threads <= bound).
+cudaError_t launch_tubes(const Args &a, int threads, int bound, int cluster, cudaStream_t s,
+                         int *nclusters_out);
+cudaError_t launch_tubes_ca(const Args &a, int threads, int bound, cudaStream_t s, int *nclusters_out);
+cudaError_t launch_tubes_cg(const Args &a, int threads, int bound, int cluster, cudaStream_t s,
+                            int *nclusters_out);
+
+// packed fields <-> tube storage; pack[b] = first packed index of tube b
+cudaError_t launch_tubes_init(int B, int max_nx, const Tube *tubes, const long long *pack, long long ps,
+                              const double *n, const double *T, const double *ux, float *f, float *h,
+                              float *prev, unsigned *status, cudaStream_t s);
+cudaError_t launch_tubes_macro(int B, int max_nx, const Tube *tubes, const long long *pack, const int *par,
+                               long long ps, long long total, const float *f0, const float *h0,
+                               const float *f1, const float *h1, double *out, unsigned *status,
+                               cudaStream_t s);
+// per-tube totals of T^00, T^0x, T^0y, T^0z, N^0: out[5 b + k]
+cudaError_t launch_tubes_totals(int B, const Tube *tubes, const int *par, long long ps, const float *f0,
+                                const float *h0, const float *f1, const float *h1, double *out,
+                                cudaStream_t s);
+
+}  // namespace batch
+
 }  // namespace rlb

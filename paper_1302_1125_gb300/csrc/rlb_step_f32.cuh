@@ -49,7 +49,9 @@ struct Geo {
     unsigned xfix;       // edge columns: clamp or ghost fix-ups (XF_*)
     int yoff[4], zoff[4];   // offsets of rows/planes at -2, -1, +1, +2 (mapped)
 };
-enum { XF_LO_CLAMP = 1, XF_LO_GHOST = 2, XF_HI_CLAMP = 4, XF_HI_GHOST = 8 };
+// XF_HI_ODD1 / XF_HI_ODD3: odd-length tube stored with one pad cell, the pair
+// holds its last cell (x0 = nx - 1) or ends two cells before it (x0 = nx - 3)
+enum { XF_LO_CLAMP = 1, XF_LO_GHOST = 2, XF_HI_CLAMP = 4, XF_HI_GHOST = 8, XF_HI_ODD1 = 16, XF_HI_ODD3 = 32 };
 
 __device__ __forceinline__ int map1(int c, int n, int lo, int hi, bool &ghost)
 {
@@ -65,19 +67,36 @@ __device__ __forceinline__ int map1(int c, int n, int lo, int hi, bool &ghost)
     return c < 0 ? 0 : n - 1;
 }
 
-template <typename P>
-__device__ __forceinline__ f2 ld2(const P *q)
+// Load kinds.  LD_NC: read-only path, for a launch that never writes the
+// populations it reads.  A persistent launch reads what it wrote in earlier
+// steps: LD_CA (cached in L1) when only threads of the same block wrote the
+// data (ordered by the block barrier), LD_CG (cached in L2 only) when other
+// blocks of the cluster wrote it on other SMs.
+enum { LD_NC = 0, LD_CA = 1, LD_CG = 2 };
+template <int LD>
+__device__ __forceinline__ f2 ld2(const float *q)
 {
-    const float2 v = __ldg(reinterpret_cast<const float2 *>(q));
+    const float2 *p = reinterpret_cast<const float2 *>(q);
+    float2 v;
+    if constexpr (LD == LD_CG) v = __ldcg(p);
+    else if constexpr (LD == LD_CA) v = __ldca(p);
+    else v = __ldg(p);
     return f2{v.x, v.y};
+}
+template <int LD>
+__device__ __forceinline__ float ld1(const float *q)
+{
+    if constexpr (LD == LD_CG) return __ldcg(q);
+    else if constexpr (LD == LD_CA) return __ldca(q);
+    else return __ldg(q);
 }
 
 // the pair of cells (x0, x0+1) at element offset `off` from idx0
-template <bool VEC2>
+template <bool VEC2, int LD = LD_NC>
 __device__ __forceinline__ f2 ldpair(const float *q, const Geo &g, int off)
 {
-    if constexpr (VEC2) return ld2(q + g.idx0 + off);
-    else return f2{__ldg(q + g.idx0 + off), __ldg(q + g.idx1 + off)};
+    if constexpr (VEC2) return ld2<LD>(q + g.idx0 + off);
+    else return f2{ld1<LD>(q + g.idx0 + off), ld1<LD>(q + g.idx1 + off)};
 }
 
 template <bool VEC2>
@@ -92,7 +111,7 @@ __device__ __forceinline__ void stpair(float *q, const Geo &g, f2 v)
 }
 
 // one value of the x-stencil through the boundary map (odd nx only)
-__device__ __noinline__ float xval_mapped(const float *q, int idx0, int x0, int k, const StepParams &p,
+static __device__ __noinline__ float xval_mapped(const float *q, int idx0, int x0, int k, const StepParams &p,
                                           float ghost)
 {
     bool gh;
@@ -103,18 +122,20 @@ __device__ __noinline__ float xval_mapped(const float *q, int idx0, int x0, int 
 // x0-2 .. x0+3 of one plane.  With even nx every thread loads three aligned
 // pairs; periodic edges wrap to aligned pairs, and the clamped (open) or ghost
 // (inlet) positions of the two edge columns are patched afterwards.
-template <bool VEC2>
+template <bool VEC2, int LD>
 __device__ __forceinline__ void xstencil(const float *q, const Geo &g, const StepParams &p, float ghost,
                                          float (&v)[6])
 {
     if constexpr (VEC2) {
-        const f2 a = ld2(q + g.idx0 + g.oa), b = ld2(q + g.idx0), c = ld2(q + g.idx0 + g.oc);
+        const f2 a = ld2<LD>(q + g.idx0 + g.oa), b = ld2<LD>(q + g.idx0), c = ld2<LD>(q + g.idx0 + g.oc);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
         if (g.xfix) {
             if (g.xfix & XF_LO_CLAMP) v[1] = v[0];
             if (g.xfix & XF_LO_GHOST) { v[0] = ghost; v[1] = ghost; }
             if (g.xfix & XF_HI_CLAMP) { v[4] = v[3]; v[5] = v[3]; }
             if (g.xfix & XF_HI_GHOST) { v[4] = ghost; v[5] = ghost; }
+            if (g.xfix & XF_HI_ODD1) { v[3] = v[2]; v[4] = v[2]; v[5] = v[2]; }
+            if (g.xfix & XF_HI_ODD3) v[5] = v[4];
         }
     } else {
 #pragma unroll
@@ -307,7 +328,7 @@ __device__ __forceinline__ float tau1(float P, float n, float eta_over_s)
 }
 
 // streaming increment of population I along axis A for the pair (+ bulk lap)
-template <bool IS_F, int I, int A, bool VEC2>
+template <bool IS_F, int I, int A, bool VEC2, int LD>
 __device__ __forceinline__ void axis2(const float *q, const Geo &g, const StepParams &p, const float (&xv)[6],
                                       f2 C, float k1, float k2, float hl, f2 &inc, f2 &lap)
 {
@@ -333,28 +354,28 @@ __device__ __forceinline__ void axis2(const float *q, const Geo &g, const StepPa
         }
     } else {
         if constexpr (c > 0) {
-            const f2 Aq = ldpair<VEC2>(q, g, off_of<A>(g, p, -2)), B = ldpair<VEC2>(q, g, off_of<A>(g, p, -1));
-            const f2 Dq = ldpair<VEC2>(q, g, off_of<A>(g, p, 1));
+            const f2 Aq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -2)), B = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -1));
+            const f2 Dq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 1));
             const f2 d0 = B - Aq, d1 = C - B, d2 = Dq - C;
             const f2 Dv = fma2(bc(hl), mm(d2, d1) - mm(d1, d0), d1);
             inc = fma2(bc(-k), Dv, inc);
             if constexpr (need_lap) lap = lap + (d2 - d1);
         } else if constexpr (c < 0) {
-            const f2 B = ldpair<VEC2>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2>(q, g, off_of<A>(g, p, 1));
-            const f2 Eq = ldpair<VEC2>(q, g, off_of<A>(g, p, 2));
+            const f2 B = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 1));
+            const f2 Eq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 2));
             const f2 e0 = C - B, e1 = Dq - C, e2 = Eq - Dq;
             const f2 Dv = fma2(bc(-hl), mm(e1, e2) - mm(e0, e1), e1);
             inc = fma2(bc(k), Dv, inc);
             if constexpr (need_lap) lap = lap + (e1 - e0);
         } else if constexpr (need_lap) {
-            const f2 B = ldpair<VEC2>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2>(q, g, off_of<A>(g, p, 1));
+            const f2 B = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 1));
             lap = lap + ((Dq - C) - (C - B));
         }
     }
 }
 
 // f (or h) + streaming (+ bulk) of population I for the pair: the explicit part of Eq. 57
-template <int DIM, bool IS_F, int I, bool VEC2>
+template <int DIM, bool IS_F, int I, bool VEC2, int LD>
 __device__ __forceinline__ f2 streamed2(const float *q, const Geo &g, const StepParams &p, float ghost,
                                         float k1, float k2, float hl, float kb)
 {
@@ -362,17 +383,153 @@ __device__ __forceinline__ f2 streamed2(const float *q, const Geo &g, const Step
     float xv[6];
     f2 C;
     if constexpr (xneed) {
-        xstencil<VEC2>(q, g, p, ghost, xv);
+        xstencil<VEC2, LD>(q, g, p, ghost, xv);
         C = mk(xv[2], xv[3]);
     } else {
-        C = ldpair<VEC2>(q, g, 0);
+        C = ldpair<VEC2, LD>(q, g, 0);
     }
     f2 inc = bc(0.0f), lap = bc(0.0f);
-    if constexpr (xneed) axis2<IS_F, I, 0, VEC2>(q, g, p, xv, C, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 1) axis2<IS_F, I, 1, VEC2>(q, g, p, xv, C, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 2) axis2<IS_F, I, 2, VEC2>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (xneed) axis2<IS_F, I, 0, VEC2, LD>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 1) axis2<IS_F, I, 1, VEC2, LD>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 2) axis2<IS_F, I, 2, VEC2, LD>(q, g, p, xv, C, k1, k2, hl, inc, lap);
     if constexpr (IS_F && I != 0) inc = fma2(bc(kb), lap, inc);
     return C + inc;
+}
+
+// The update of one pair of cells (Eq. 57 for f and h), shared by the grid
+// kernel and the batched tube kernel.  eos = eta/s and kb = the bulk
+// prefactor of the cell's grid or tube.
+template <int DIM, bool EULER, bool VEC2, int LD = LD_NC>
+__device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
+                                            const float *__restrict__ f, const float *__restrict__ h,
+                                            float *__restrict__ fo, float *__restrict__ ho,
+                                            float *__restrict__ prev, long long ps)
+{
+    const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim;
+
+    if constexpr (!EULER) {
+        // raw sums of the local populations: S = sum f, V_a = sum c_a f
+        // (double-float), Sh = sum h
+        df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
+        for_pops(RLB_F32_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const f2 v = ldpair<VEC2, LD>(f + I * ps, g, 0);
+            acc(S, v);
+            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
+            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
+            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
+            acc(Hs, ldpair<VEC2, LD>(h + I * ps, g, 0));
+        });
+        const f2 Sh = Hs.hi + Hs.lo;
+        bool ok0, ok1;
+        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
+
+        f2 kap;
+        {
+            float t0, t1;
+            if (p.f_tau_override > 0.0f) {
+                t0 = t1 = p.f_tau_override;
+            } else {
+                t0 = tau1(mt.P.x, mt.n.x, eos);
+                t1 = tau1(mt.P.y, mt.n.y, eos);
+            }
+            const float kw = p.f_kw;
+            const float w0 = kw / t0, w1 = kw / t1;
+            kap = f2{w0 / (1.0f + w0), w1 / (1.0f + w1)};
+        }
+
+        // the previous level holds the raw moment sums of time t - dt, so the
+        // targets of 2 f^eq(t) - f^eq(t - dt) are exact: T = 2 S(t) - S(t - dt)
+        const f2 Sp = ldpair<VEC2, LD>(prev + 0 * ps, g, 0);
+        const f2 Vpx = ldpair<VEC2, LD>(prev + 1 * ps, g, 0);
+        const f2 Vpy = ldpair<VEC2, LD>(prev + 2 * ps, g, 0);
+        const f2 Vpz = ldpair<VEC2, LD>(prev + 3 * ps, g, 0);
+        const f2 Shp = ldpair<VEC2, LD>(prev + 4 * ps, g, 0);
+        const Mac2 mp = recover2f(Sp, Vpx, Vpy, Vpz, Shp);
+        const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
+        f2 Ta[3];
+        Ta[0] = fma2(bc(2.0f), Vx.hi + Vx.lo, -Vpx);
+        Ta[1] = fma2(bc(2.0f), Vy.hi + Vy.lo, -Vpy);
+        Ta[2] = fma2(bc(2.0f), Vz.hi + Vz.lo, -Vpz);
+
+        {
+            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
+            coef_f2(mt, K0, Kb, Kd, Ko);
+            coef_f2(mp, L0, Lb, Ld, Lo);
+            K0 = fma2(bc(2.0f), K0, -L0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
+                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
+                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
+            }
+            const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), T0, Ta);
+            for_pops(RLB_F32_POPS, [&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                const f2 pre = streamed2<DIM, true, I, VEC2, LD>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
+                stpair<VEC2>(fo + I * ps, g, fma2(kap, eq2<I>(ef) - pre, pre));
+            });
+        }
+        {
+            const f2 T0h = fma2(bc(2.0f), Sh, -Shp);
+            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
+            coef_h2(mt, K0, Kb, Kd, Ko);
+            coef_h2(mp, L0, Lb, Ld, Lo);
+            K0 = fma2(bc(2.0f), K0, -L0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
+                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
+                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
+            }
+            const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
+            for_pops(RLB_F32_POPS, [&](auto ic) {
+                constexpr int I = decltype(ic)::value;
+                const f2 pre = streamed2<DIM, false, I, VEC2, LD>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb);
+                stpair<VEC2>(ho + I * ps, g, fma2(kap, eq2<I>(eh) - pre, pre));
+            });
+        }
+        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
+        stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
+        stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
+        stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
+        stpair<VEC2>(prev + 4 * ps, g, Sh);
+    } else {
+        // Euler mode (Sec. III): f, h <- equilibria of the streamed state
+        df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
+        for_pops(RLB_F32_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            const f2 v = streamed2<DIM, true, I, VEC2, LD>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
+            acc(S, v);
+            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
+            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
+            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
+            acc(Hs, streamed2<DIM, false, I, VEC2, LD>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb));
+        });
+        const f2 Sh = Hs.hi + Hs.lo;
+        bool ok0, ok1;
+        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
+        const f2 Ta[3] = {Vx.hi + Vx.lo, Vy.hi + Vy.lo, Vz.hi + Vz.lo};
+        f2 K0, Kb[3], Kd[3], Ko[3];
+        coef_f2(mt, K0, Kb, Kd, Ko);
+        const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), S.hi + S.lo, Ta);
+        coef_h2(mt, K0, Kb, Kd, Ko);
+        const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), Sh, nullptr);
+        for_pops(RLB_F32_POPS, [&](auto ic) {
+            constexpr int I = decltype(ic)::value;
+            stpair<VEC2>(fo + I * ps, g, eq2<I>(ef));
+            stpair<VEC2>(ho + I * ps, g, eq2<I>(eh));
+        });
+        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
+        stpair<VEC2>(prev + 1 * ps, g, Ta[0]);
+        stpair<VEC2>(prev + 2 * ps, g, Ta[1]);
+        stpair<VEC2>(prev + 3 * ps, g, Ta[2]);
+        stpair<VEC2>(prev + 4 * ps, g, Sh);
+    }
 }
 
 template <int DIM, bool EULER, bool VEC2>
@@ -413,132 +570,7 @@ __global__ void __launch_bounds__(256, VEC2 ? 2 : 1) step_f32_kernel(const StepP
             g.zoff[k] = DIM > 2 ? (map1(z + ds[k], p.nz, p.bc_lo[2], p.bc_hi[2], gh) - z) * p.nx * p.ny : 0;
         }
     }
-    const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim, kb = p.f_kbulk;
-    const float eos = p.f_eta_over_s;
-
-    if constexpr (!EULER) {
-        // raw sums of the local populations: S = sum f, V_a = sum c_a f
-        // (double-float), Sh = sum h
-        df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
-        for_pops(RLB_F32_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            const f2 v = ldpair<VEC2>(f + I * ps, g, 0);
-            acc(S, v);
-            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
-            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
-            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
-            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
-            acc(Hs, ldpair<VEC2>(h + I * ps, g, 0));
-        });
-        const f2 Sh = Hs.hi + Hs.lo;
-        bool ok0, ok1;
-        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
-        if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
-
-        f2 kap;
-        {
-            float t0, t1;
-            if (p.f_tau_override > 0.0f) {
-                t0 = t1 = p.f_tau_override;
-            } else {
-                t0 = tau1(mt.P.x, mt.n.x, eos);
-                t1 = tau1(mt.P.y, mt.n.y, eos);
-            }
-            const float kw = p.f_kw;
-            const float w0 = kw / t0, w1 = kw / t1;
-            kap = f2{w0 / (1.0f + w0), w1 / (1.0f + w1)};
-        }
-
-        // the previous level holds the raw moment sums of time t - dt, so the
-        // targets of 2 f^eq(t) - f^eq(t - dt) are exact: T = 2 S(t) - S(t - dt)
-        const f2 Sp = ldpair<VEC2>(prev + 0 * ps, g, 0);
-        const f2 Vpx = ldpair<VEC2>(prev + 1 * ps, g, 0);
-        const f2 Vpy = ldpair<VEC2>(prev + 2 * ps, g, 0);
-        const f2 Vpz = ldpair<VEC2>(prev + 3 * ps, g, 0);
-        const f2 Shp = ldpair<VEC2>(prev + 4 * ps, g, 0);
-        const Mac2 mp = recover2f(Sp, Vpx, Vpy, Vpz, Shp);
-        const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
-        f2 Ta[3];
-        Ta[0] = fma2(bc(2.0f), Vx.hi + Vx.lo, -Vpx);
-        Ta[1] = fma2(bc(2.0f), Vy.hi + Vy.lo, -Vpy);
-        Ta[2] = fma2(bc(2.0f), Vz.hi + Vz.lo, -Vpz);
-
-        {
-            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
-            coef_f2(mt, K0, Kb, Kd, Ko);
-            coef_f2(mp, L0, Lb, Ld, Lo);
-            K0 = fma2(bc(2.0f), K0, -L0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
-                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
-                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
-            }
-            const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), T0, Ta);
-            for_pops(RLB_F32_POPS, [&](auto ic) {
-                constexpr int I = decltype(ic)::value;
-                const f2 pre = streamed2<DIM, true, I, VEC2>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
-                stpair<VEC2>(fo + I * ps, g, fma2(kap, eq2<I>(ef) - pre, pre));
-            });
-        }
-        {
-            const f2 T0h = fma2(bc(2.0f), Sh, -Shp);
-            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
-            coef_h2(mt, K0, Kb, Kd, Ko);
-            coef_h2(mp, L0, Lb, Ld, Lo);
-            K0 = fma2(bc(2.0f), K0, -L0);
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
-                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
-                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
-            }
-            const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
-            for_pops(RLB_F32_POPS, [&](auto ic) {
-                constexpr int I = decltype(ic)::value;
-                const f2 pre = streamed2<DIM, false, I, VEC2>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb);
-                stpair<VEC2>(ho + I * ps, g, fma2(kap, eq2<I>(eh) - pre, pre));
-            });
-        }
-        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
-        stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
-        stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
-        stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
-        stpair<VEC2>(prev + 4 * ps, g, Sh);
-    } else {
-        // Euler mode (Sec. III): f, h <- equilibria of the streamed state
-        df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
-        for_pops(RLB_F32_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            const f2 v = streamed2<DIM, true, I, VEC2>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
-            acc(S, v);
-            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
-            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
-            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
-            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
-            acc(Hs, streamed2<DIM, false, I, VEC2>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb));
-        });
-        const f2 Sh = Hs.hi + Hs.lo;
-        bool ok0, ok1;
-        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
-        if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
-        const f2 Ta[3] = {Vx.hi + Vx.lo, Vy.hi + Vy.lo, Vz.hi + Vz.lo};
-        f2 K0, Kb[3], Kd[3], Ko[3];
-        coef_f2(mt, K0, Kb, Kd, Ko);
-        const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), S.hi + S.lo, Ta);
-        coef_h2(mt, K0, Kb, Kd, Ko);
-        const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), Sh, nullptr);
-        for_pops(RLB_F32_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            stpair<VEC2>(fo + I * ps, g, eq2<I>(ef));
-            stpair<VEC2>(ho + I * ps, g, eq2<I>(eh));
-        });
-        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
-        stpair<VEC2>(prev + 1 * ps, g, Ta[0]);
-        stpair<VEC2>(prev + 2 * ps, g, Ta[1]);
-        stpair<VEC2>(prev + 3 * ps, g, Ta[2]);
-        stpair<VEC2>(prev + 4 * ps, g, Sh);
-    }
+    update_pair<DIM, EULER, VEC2>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho, prev, ps);
 }
 
 }  // namespace f32

@@ -37,6 +37,14 @@ class rlb_options(C.Structure):
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
 
 
+class rlb_batch_tuning(C.Structure):
+    _fields_ = [("threads", C.c_int), ("bound", C.c_int), ("cluster", C.c_int),
+                ("pairs_per_thread", C.c_int), ("ms", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class RLBError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"{status_string(status)}: {message}")
@@ -90,6 +98,35 @@ def lib() -> C.CDLL:
         L.rlb_status_string.restype = C.c_char_p
         L.rlb_conserved_totals_noalloc.argtypes = [vp, vp, C.c_int, C.c_longlong, C.c_int, vp, vp]
         L.rlb_conserved_totals_noalloc.restype = C.c_int
+        ip, llp, tp = C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(rlb_batch_tuning)
+        L.rlb_batch_create.argtypes = [C.c_int, ip, dp, dp, C.c_int, C.POINTER(rlb_options), C.POINTER(vp)]
+        L.rlb_batch_create.restype = C.c_int
+        L.rlb_batch_init.argtypes = [vp, vp, vp, vp, C.c_int]
+        L.rlb_batch_init.restype = C.c_int
+        L.rlb_batch_step.argtypes = [vp, llp]
+        L.rlb_batch_step.restype = C.c_int
+        L.rlb_batch_macroscopic.argtypes = [vp, vp, C.c_int]
+        L.rlb_batch_macroscopic.restype = C.c_int
+        L.rlb_batch_totals.argtypes = [vp, dp]
+        L.rlb_batch_totals.restype = C.c_int
+        L.rlb_batch_plan.argtypes = [C.c_int, ip, llp, tp, C.c_int, ip, ip, ip, ip, llp]
+        L.rlb_batch_plan.restype = C.c_int
+        L.rlb_batch_autotune.argtypes = [vp, llp, C.c_int, tp, C.c_int, ip, tp]
+        L.rlb_batch_autotune.restype = C.c_int
+        L.rlb_batch_set_tuning.argtypes = [vp, tp]
+        L.rlb_batch_set_tuning.restype = C.c_int
+        L.rlb_batch_get_tuning.argtypes = [vp, tp, ip]
+        L.rlb_batch_get_tuning.restype = C.c_int
+        L.rlb_batch_set_stream.argtypes = [vp, vp]
+        L.rlb_batch_set_stream.restype = C.c_int
+        L.rlb_batch_total_cells.argtypes = [vp]
+        L.rlb_batch_total_cells.restype = C.c_longlong
+        L.rlb_batch_launch_count.argtypes = [vp]
+        L.rlb_batch_launch_count.restype = C.c_longlong
+        L.rlb_batch_destroy.argtypes = [vp]
+        L.rlb_batch_destroy.restype = None
+        L.rlb_batch_last_error.argtypes = [vp]
+        L.rlb_batch_last_error.restype = C.c_char_p
         _lib = L
     return _lib
 
@@ -294,6 +331,135 @@ class Grid:
         if self.ctx:
             rlb_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# Batched tubes
+# ---------------------------------------------------------------------------
+
+def batch_last_error(b=None) -> str:
+    return lib().rlb_batch_last_error(b).decode()
+
+
+def _bcheck(status: int, b=None):
+    if status != RLB_OK:
+        raise RLBError(status, batch_last_error(b))
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, np.int32)
+
+
+def _i64(a):
+    return np.ascontiguousarray(a, np.int64)
+
+
+def rlb_batch_plan(nx, nsteps, tuning, nclusters):
+    """Host-side job plan (see rlb.h): (order, jobs[njobs, 4], cl_start, critical)."""
+    nx, st = _i32(nx), _i64(nsteps)
+    B = nx.size
+    order = np.zeros(B, np.int32)
+    jobs = np.zeros(4 * B, np.int32)
+    cl = np.zeros(int(nclusters) + 1, np.int32)
+    nj, crit = C.c_int(), C.c_longlong()
+    ip, llp = C.POINTER(C.c_int), C.POINTER(C.c_longlong)
+    _bcheck(lib().rlb_batch_plan(B, nx.ctypes.data_as(ip), st.ctypes.data_as(llp), C.byref(tuning),
+                                 int(nclusters), order.ctypes.data_as(ip), jobs.ctypes.data_as(ip),
+                                 C.byref(nj), cl.ctypes.data_as(ip), C.byref(crit)))
+    return order, jobs[:4 * nj.value].reshape(-1, 4), cl, crit.value
+
+
+class Batch:
+    """B independent 1-D tubes advanced by one persistent launch (FP32 storage)."""
+
+    def __init__(self, nx, eta_over_s, zeta_over_s, *, limiter=LIMITER_MINMOD, dt_over_dx=0.15,
+                 tau_override=0.0, alpha_override=-1.0, stream="current"):
+        self.nx = _i32(nx)
+        self.B = int(self.nx.size)
+        self.eta = np.ascontiguousarray(eta_over_s, np.float64)
+        self.zeta = np.ascontiguousarray(zeta_over_s, np.float64)
+        s = _current_stream() if stream == "current" else stream
+        self._opts = make_options(dt_over_dx, tau_override, alpha_override, 0, FP32_STORAGE, s)
+        h = C.c_void_p()
+        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+        _bcheck(lib().rlb_batch_create(self.B, self.nx.ctypes.data_as(ip), self.eta.ctypes.data_as(dp),
+                                       self.zeta.ctypes.data_as(dp), int(limiter), C.byref(self._opts),
+                                       C.byref(h)))
+        self.b = h
+        self.total = int(lib().rlb_batch_total_cells(self.b))
+        self.offsets = np.zeros(self.B + 1, np.int64)
+        self.offsets[1:] = np.cumsum(self.nx)
+
+    @classmethod
+    def from_spec(cls, spec, **kw):
+        return cls(spec.nx, spec.eta_over_s, spec.zeta_over_s, dt_over_dx=spec.dt_over_dx,
+                   alpha_override=spec.alpha, **kw)
+
+    def init(self, n, T, ux):
+        ptrs, keep, ondev = [], [], None
+        for a in (n, T, ux):
+            p, d, k = _as_f64(a, self.total)
+            ondev = d if ondev is None else ondev
+            if d != ondev:
+                raise ValueError("all fields must be on the same side (host or device)")
+            ptrs.append(p)
+            keep.append(k)
+        _bcheck(lib().rlb_batch_init(self.b, *ptrs, ondev), self.b)
+        return self
+
+    def step(self, nsteps):
+        st = _i64(np.broadcast_to(np.asarray(nsteps, np.int64), (self.B,)))
+        _bcheck(lib().rlb_batch_step(self.b, st.ctypes.data_as(C.POINTER(C.c_longlong))), self.b)
+        return self
+
+    def macroscopic(self, device=True):
+        """(6, total) float64, packed: n, e, u_x, u_y, u_z, gamma"""
+        if device:
+            torch = _torch()
+            out = torch.empty((6, self.total), dtype=torch.float64, device="cuda")
+            _bcheck(lib().rlb_batch_macroscopic(self.b, out.data_ptr(), 1), self.b)
+            return out
+        out = np.empty((6, self.total))
+        _bcheck(lib().rlb_batch_macroscopic(self.b, out.ctypes.data, 0), self.b)
+        return out
+
+    def totals(self):
+        """(B, 5): per-tube T^00, T^0x, T^0y, T^0z, N^0"""
+        out = np.zeros(5 * self.B)
+        _bcheck(lib().rlb_batch_totals(self.b, out.ctypes.data_as(C.POINTER(C.c_double))), self.b)
+        return out.reshape(self.B, 5)
+
+    def tuning(self):
+        t, n = rlb_batch_tuning(), C.c_int()
+        _bcheck(lib().rlb_batch_get_tuning(self.b, C.byref(t), C.byref(n)), self.b)
+        return t, n.value
+
+    def set_tuning(self, threads, bound, cluster, pairs_per_thread=1):
+        t = rlb_batch_tuning(int(threads), int(bound), int(cluster), int(pairs_per_thread), 0.0)
+        _bcheck(lib().rlb_batch_set_tuning(self.b, C.byref(t)), self.b)
+
+    def autotune(self, nsteps, divisor=16, max_trials=64):
+        st = _i64(np.broadcast_to(np.asarray(nsteps, np.int64), (self.B,)))
+        trials = (rlb_batch_tuning * max_trials)()
+        n, best = C.c_int(), rlb_batch_tuning()
+        _bcheck(lib().rlb_batch_autotune(self.b, st.ctypes.data_as(C.POINTER(C.c_longlong)), int(divisor),
+                                         trials, int(max_trials), C.byref(n), C.byref(best)), self.b)
+        return best, [trials[i] for i in range(min(n.value, max_trials))]
+
+    @property
+    def launches(self) -> int:
+        return int(lib().rlb_batch_launch_count(self.b))
+
+    def close(self):
+        if self.b:
+            lib().rlb_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

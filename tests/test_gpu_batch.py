@@ -1,0 +1,231 @@
+"""The batched-tube path (rlb_batch_*) on the GPU.
+
+* Against the single-grid FP32-storage path: tube b of a batch, stepped by
+  the persistent kernel, must equal bit for bit the same tube run alone
+  through rlb_create / rlb_step (nx_b x 1 x 1, outflow ends): the per-cell
+  arithmetic is the same, only the work division differs.  Checked for odd
+  and even lengths down to 1 cell, zero-step tubes, step counts split over
+  calls, and every kind of launch shape (block, cluster of 2/4/8 blocks,
+  grouped jobs).
+* Against the FP64 oracle: per-tube L1 relative error <= 1e-4, as for the
+  FP32 form of the grid.
+* The full 512-tube sweep (4 Nx steps per tube) runs in one call; a sample of
+  tubes is compared with their single-grid runs and, for the short ones,
+  with the oracle.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1302_1125_gb300 import rlb
+from paper_1302_1125_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+FP32_L1_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1302_1125_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+
+
+def small_spec(alpha=0.2, seed=3):
+    """ten tubes of mixed length (odd and even, down to one cell)"""
+    nx = np.array([64, 37, 130, 5, 1, 2, 3, 256, 97, 300], np.int32)
+    rng = np.random.default_rng(seed)
+    B_ = nx.size
+    off = np.zeros(B_ + 1, np.int64)
+    off[1:] = np.cumsum(nx)
+    return W.BatchSpec(nx, rng.uniform(0.01, 0.5, B_), rng.uniform(0.0, 10.0, B_),
+                       np.exp(rng.uniform(math.log(2.0), math.log(40.0), B_)), rng.uniform(1.0, 1.5, B_),
+                       4 * nx.astype(np.int64), off, dt_over_dx=0.15, alpha=alpha)
+
+
+def run_batch(spec, steps_list, tuning=None):
+    b = rlb.Batch.from_spec(spec)
+    if tuning is not None:
+        b.set_tuning(*tuning)
+    b.init(*spec.fields())
+    for st in steps_list:
+        b.step(st)
+    out = b.macroscopic(device=False)
+    return b, out
+
+
+def run_single(spec, i, steps, precision=rlb.FP32_STORAGE):
+    o, m = int(spec.offsets[i]), int(spec.nx[i])
+    n, T, ux = (a[o:o + m] for a in spec.fields())
+    out = rlb.BC_OUTFLOW, rlb.BC_PERIODIC, rlb.BC_PERIODIC
+    g = rlb.Grid(m, bc_lo=out, bc_hi=out, eta_over_s=float(spec.eta_over_s[i]),
+                 zeta_over_s=float(spec.zeta_over_s[i]), dt_over_dx=spec.dt_over_dx, alpha_override=spec.alpha,
+                 precision=precision)
+    z = np.zeros(m)
+    g.init(n, T, ux, z, z)
+    g.step(int(steps))
+    res = g.macroscopic(device=False)
+    tot = g.totals()
+    g.close()
+    return res, tot
+
+
+def tube(out, spec, i):
+    o, m = int(spec.offsets[i]), int(spec.nx[i])
+    return out[:, o:o + m]
+
+
+@pytest.mark.parametrize("alpha", [0.2, -1.0])
+def test_batch_equals_single_grid_runs_bit_for_bit(alpha):
+    spec = small_spec(alpha)
+    steps = np.array([40, 17, 0, 9, 5, 6, 7, 60, 33, 51])
+    b, out = run_batch(spec, [steps])
+    for i in range(spec.B):
+        ref, _ = run_single(spec, i, steps[i])
+        got = tube(out, spec, i)
+        assert np.array_equal(got, ref), (i, np.max(np.abs(got - ref)))
+    b.close()
+
+
+@pytest.mark.parametrize("tuning", [(32, 256, 1, 1), (64, 512, 2, 1), (128, 384, 4, 1), (32, 256, 8, 2),
+                                    (256, 256, 1, 4), (512, 512, 2, 1)])
+def test_every_launch_shape_gives_the_same_state(tuning):
+    spec = small_spec()
+    steps = np.array([40, 17, 0, 9, 5, 6, 7, 60, 33, 51])
+    _, ref = run_batch(spec, [steps], (256, 256, 1, 1))
+    b, got = run_batch(spec, [steps], tuning)
+    t, ncl = b.tuning()
+    assert (t.threads, t.bound, t.cluster, t.pairs_per_thread) == tuning and ncl >= 1
+    assert np.array_equal(got, ref)
+    b.close()
+
+
+def test_steps_split_over_calls_and_graph_replays():
+    spec = small_spec()
+    a = np.array([3, 5, 0, 2, 1, 0, 4, 8, 1, 7])
+    c = np.array([4, 0, 7, 2, 0, 3, 4, 8, 2, 1])
+    b = rlb.Batch.from_spec(spec).init(*spec.fields())
+    launches = b.launches
+    b.step(a)
+    b.step(c)
+    b.step(c)         # same counts: the uploaded plan and the graph are reused
+    b.step(0)         # nothing to do: no launch
+    assert b.launches == launches + 3
+    out = b.macroscopic(device=False)
+    for i in range(spec.B):
+        ref, _ = run_single(spec, i, a[i] + 2 * c[i])
+        assert np.array_equal(tube(out, spec, i), ref), i
+    b.close()
+
+
+def test_device_and_host_fields_agree():
+    spec = small_spec()
+    b1 = rlb.Batch.from_spec(spec).init(*spec.fields())
+    b2 = rlb.Batch.from_spec(spec).init(*[torch.as_tensor(x, device="cuda") for x in spec.fields()])
+    b1.step(11)
+    b2.step(11)
+    assert torch.equal(b1.macroscopic(device=True), b2.macroscopic(device=True))
+    b1.close()
+    b2.close()
+
+
+def test_batch_totals_match_the_grid_totals():
+    spec = small_spec()
+    steps = np.array([40, 17, 0, 9, 5, 6, 7, 60, 33, 51])
+    b, _ = run_batch(spec, [steps])
+    tot = b.totals()
+    for i in range(spec.B):
+        _, ref = run_single(spec, i, steps[i])
+        assert np.allclose(tot[i], ref, rtol=1e-12, atol=1e-12 * abs(ref[0])), (i, tot[i], ref)
+    b.close()
+
+
+def oracle_tube(orc, spec, i, steps):
+    o, m = int(spec.offsets[i]), int(spec.nx[i])
+    n, T, ux = (a[o:o + m] for a in spec.fields())
+    p = orc.Params(nx=m, ny=1, nz=1, bc_lo=(1, 0, 0), bc_hi=(1, 0, 0), dt=spec.dt_over_dx,
+                   eta_over_s=float(spec.eta_over_s[i]), zeta_over_s=float(spec.zeta_over_s[i]),
+                   tau_override=0.0, alpha_override=spec.alpha)
+    z = np.zeros(m)
+    s = orc.init(p, n, T, ux, z, z)
+    orc.step(s, int(steps))
+    assert s.nonphysical == 0
+    return orc.macroscopic(s)
+
+
+def l1(got, ref):
+    return np.sum(np.abs(got - ref)) / max(np.sum(np.abs(ref)), 1e-300)
+
+
+def test_batch_against_the_fp64_oracle(orc):
+    spec = small_spec()
+    steps = 4 * spec.nx.astype(np.int64)
+    b, out = run_batch(spec, [steps], (64, 512, 2, 1))
+    for i in range(spec.B):
+        ref = oracle_tube(orc, spec, i, steps[i])
+        got = tube(out, spec, i)
+        for k, name in ((0, "n"), (1, "e")):
+            assert l1(got[k], ref[k]) <= FP32_L1_TOL, (i, name, l1(got[k], ref[k]))
+        # u_x against the scale of gamma u (zero at rest)
+        du = np.sum(np.abs(got[2] - ref[2])) / max(np.sum(np.abs(ref[5])), 1e-300)
+        assert du <= FP32_L1_TOL, (i, "u_x", du)
+    b.close()
+
+
+def test_autotune_keeps_the_state_and_picks_a_measured_shape():
+    spec = small_spec()
+    steps = np.array([40, 17, 3, 9, 5, 6, 7, 60, 33, 51])
+    b = rlb.Batch.from_spec(spec).init(*spec.fields())
+    b.step(steps)
+    before = b.macroscopic(device=False)
+    best, trials = b.autotune(steps, divisor=4)
+    assert best.ms > 0.0 and len(trials) >= 10
+    assert best.ms == min(t.ms for t in trials if t.ms > 0.0)
+    t, ncl = b.tuning()
+    assert (t.threads, t.bound, t.cluster, t.pairs_per_thread) == \
+        (best.threads, best.bound, best.cluster, best.pairs_per_thread) and ncl >= 1
+    assert np.array_equal(b.macroscopic(device=False), before)
+    b.step(steps)
+    ref = run_batch(spec, [steps, steps])[1]
+    assert np.array_equal(b.macroscopic(device=False), ref)
+    b.close()
+
+
+def test_non_physical_tube_is_reported_and_cleared():
+    spec = small_spec()
+    n, T, ux = spec.fields()
+    bad = ux.copy()
+    o, m = int(spec.offsets[7]), int(spec.nx[7])
+    bad[o:o + m // 2] = 0.995           # a gamma = 10 slab into gas at rest
+    b = rlb.Batch.from_spec(spec).init(n, T, bad)
+    with pytest.raises(rlb.RLBError) as e:
+        b.step(6)
+    assert e.value.status == rlb.RLB_E_NONPHYSICAL
+    b.init(n, T, ux)
+    b.step(3)                           # the status was cleared
+    b.close()
+
+
+def test_full_512_tube_sweep(orc):
+    """The 512-tube sweep from seed 1234, every tube 4 Nx steps in one call;
+    sampled tubes against their single-grid runs (bit for bit) and the two
+    shortest against the oracle."""
+    spec = W.batch_tubes()
+    b = rlb.Batch.from_spec(spec).init(*spec.fields())
+    b.step(spec.steps)
+    out = b.macroscopic(device=False)
+    assert np.all(np.isfinite(out))
+    order = np.argsort(spec.nx)
+    sample = [int(order[0]), int(order[len(order) // 2]), int(order[-1])]
+    for i in sample:
+        ref, _ = run_single(spec, i, spec.steps[i])
+        assert np.array_equal(tube(out, spec, i), ref), i
+    for i in order[:2]:
+        ref = oracle_tube(orc, spec, int(i), spec.steps[i])
+        got = tube(out, spec, int(i))
+        for k in (0, 1):
+            assert l1(got[k], ref[k]) <= FP32_L1_TOL, (int(i), k, l1(got[k], ref[k]))
+    b.close()
