@@ -6,7 +6,9 @@ population storage with FP64 moments and recovery; a step is one time step
 of the whole grid (every cell: minmod streaming of 38 populations, bulk
 Laplacian, moments, Landau recovery, equilibria, implicit update).  The FP64
 form is timed on the same grid for the FP32/FP64 ratio, and the FP32 form's
-L1 error against the FP64 form is measured on the 800-cell tube.
+L1 error against the FP64 form is measured on the 800-cell tube.  The
+512-tube batched sweep (one persistent launch) is reported under "batch",
+next to a sample of the same tubes run one by one.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -38,28 +40,31 @@ BYTES_FP32 = 38 * 4 * 2 + 5 * 4 * 2     # 344
 BYTES_FP64 = 38 * 8 * 2 + 5 * 8 * 2     # 688
 
 
-def csrc_hash() -> str:
+def csrc_hash(files=None) -> str:
+    """sha256 (first 16 hex) of the named kernel sources (all of csrc/ if None)"""
     import hashlib
     d = os.path.join(ROOT, "paper_1302_1125_gb300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
+    for f in sorted(files if files else os.listdir(d)):
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(summary: str, cells: int):
-    """DRAM bytes per launch from the committed ncu summary of this kernel,
-    scaled to `cells`, or None if the kernel sources changed since the capture"""
+def profiled_traffic(summary: str, units: float):
+    """DRAM bytes per launch from the committed ncu summary of a kernel (bytes
+    per unit x units), or None if that kernel's sources changed since the
+    capture"""
     try:
         text = open(os.path.join(ROOT, "profiles", summary)).read()
     except OSError:
         return None
-    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(("csrc_sha256:",
-                                                                                 "traffic_bytes_per_cell:")))
-    if fields.get("csrc_sha256", "").split()[0:1] != [csrc_hash()]:
+    keys = ("csrc_sha256:", "csrc_files:", "traffic_bytes_per_cell:")
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(keys))
+    files = fields.get("csrc_files", "").split() or None
+    if fields.get("csrc_sha256", "").split()[0:1] != [csrc_hash(files)]:
         return None
-    return float(fields["traffic_bytes_per_cell"].split()[0]) * cells
+    return float(fields["traffic_bytes_per_cell"].split()[0]) * units
 
 
 def peaks():
@@ -238,6 +243,86 @@ def l1_fp32_vs_fp64(torch):
             "u_x": float(np.abs(a[2] - b[2]).sum() / np.abs(b[2]).sum())}
 
 
+def batch_sweep(torch, rlb, W, hbm_peak, device_index):
+    """The 512-tube sweep (seed 1234, each tube 4 Nx steps) in one persistent
+    launch with the autotuned shape, and a sample of the same tubes run one by
+    one through the single-grid path (FP64 and FP32 storage) for comparison."""
+    spec = W.batch_tubes()
+    updates = float(np.sum(spec.nx.astype(np.float64) * spec.steps))
+    b = rlb.Batch.from_spec(spec)
+    b.init(*spec.fields())
+    best, trials = b.autotune(spec.steps, divisor=32)
+    for _ in range(3):                      # warm-up launches (graph capture included)
+        b.step(np.maximum(spec.steps // 64, 1))
+    b.init(*spec.fields())
+    stream = torch.cuda.current_stream()
+    for attempt in range(2):
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(device_index) as cs:
+            torch.cuda.synchronize()
+            l0 = b.launches
+            start.record(stream)
+            b.step(spec.steps)
+            end.record(stream)
+            torch.cuda.synchronize()
+        ms = start.elapsed_time(end)
+        launches = b.launches - l0
+        clk = cs.summary()
+        if not rejected(clk):
+            break
+        b.init(*spec.fields())
+    t, ncl = b.tuning()
+    b.close()
+    value = updates / (ms * 1e-3) / 1e6
+    achieved = BYTES_FP32 * updates / (ms * 1e-3) / 1e9
+
+    # the same tubes run separately: every 64th tube by length, Nx steps each
+    # (a quarter of the sweep's count; the cost per step does not change)
+    order = np.argsort(spec.nx, kind="stable")
+    sample = [int(i) for i in order[::64]]
+    out = rlb.BC_OUTFLOW, rlb.BC_PERIODIC, rlb.BC_PERIODIC
+    sep = {}
+    for name, prec in (("fp64", rlb.FP64), ("fp32_storage", rlb.FP32_STORAGE)):
+        tot_ms, tot_upd = 0.0, 0.0
+        for i in sample:
+            o, m = int(spec.offsets[i]), int(spec.nx[i])
+            n, T, ux = (a[o:o + m] for a in spec.fields())
+            g = rlb.Grid(m, bc_lo=out, bc_hi=out, eta_over_s=float(spec.eta_over_s[i]),
+                         zeta_over_s=float(spec.zeta_over_s[i]), dt_over_dx=spec.dt_over_dx,
+                         alpha_override=spec.alpha, precision=prec)
+            z = np.zeros(m)
+            g.init(n, T, ux, z, z)
+            g.step(3)
+            g.init(n, T, ux, z, z)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            g.step(m)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            tot_ms += s0.elapsed_time(s1)
+            tot_upd += m * float(m)
+            g.close()
+        sep[name] = {"value": tot_upd / (tot_ms * 1e-3) / 1e6, "unit": UNIT,
+                     "sample": f"{len(sample)} of the 512 tubes (every 64th by length), Nx steps each "
+                               f"({tot_upd:.3g} cell updates), each alone through rlb_create/rlb_step, "
+                               f"one launch per step"}
+    return {"workload": "batch_tubes: 512 1-D shock tubes from seed 1234, Nx log-uniform in [256, 8192], "
+                        "eta/s U[0.01, 0.5], pressure ratio log-U[2, 40], gamma_L U[1, 1.5], alpha 0.2, "
+                        "dt/dx 0.15, each tube 4 Nx steps, FP32 storage",
+            "tubes": int(spec.B), "cells": int(spec.offsets[-1]), "cell_updates": updates,
+            "value": value, "unit": UNIT, "ms": ms, "gpu_launches": launches,
+            "tuning": {k: v for k, v in t.as_dict().items() if k != "ms"}, "resident_clusters": ncl,
+            "autotune_trials": len(trials),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak,
+                         "note": f"{BYTES_FP32} algorithmic bytes per cell update; the working set of the "
+                                 "tubes in flight is largely L2-resident"},
+            "separate_runs": sep,
+            "batched_over_separate_fp64": value / sep["fp64"]["value"],
+            "clocks": clk}
+
+
 def run_ours(args):
     global _dist
     import torch
@@ -303,6 +388,7 @@ def run_ours(args):
            "h2d_bytes_per_step": 5 * 8 * N / args.steps, "d2h_bytes_per_step": 6 * 8 * N / args.steps,
            "what": "pinned host n,T,u -> rlb_init -> K steps -> rlb_macroscopic to pinned host"}
 
+    batch = batch_sweep(torch, rlb, W, hbm_peak, local) if not args.no_batch else None
     if rank != 0:
         return 0
     l1 = l1_fp32_vs_fp64(torch)
@@ -331,6 +417,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": base,
+        "batch": batch,
     }
     print(json.dumps(line), flush=True)
     if _dist is not None:
@@ -344,6 +431,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-tube batched sweep")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
