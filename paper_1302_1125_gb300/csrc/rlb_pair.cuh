@@ -56,12 +56,23 @@ __device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
 }
 __device__ __forceinline__ f2 operator-(f2 a) { return f2{-a.x, -a.y}; }
 
-// minmod(a, b) = median(0, a, b): the smaller magnitude when a and b share a
-// sign, zero otherwise (Eq. 53)
+// minmod(a, b) (Eq. 53): the smaller magnitude when a and b share a sign,
+// zero otherwise.  min.xorsign.abs gives m = min(|a|, |b|) carrying the sign
+// sign(a) xor sign(b): m > 0 exactly when the signs agree, then the result is
+// m with the sign of a; otherwise max(m, 0) = 0.
+#ifndef RLB_MM_MEDIAN
 __device__ __forceinline__ float mm(float a, float b)
 {
-    return fminf(fmaxf(a, b), fmaxf(fminf(a, b), 0.0f));
+    float m;
+    asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(m) : "f"(a), "f"(b));
+    return copysignf(fmaxf(m, 0.0f), a);
 }
+#else
+__device__ __forceinline__ float mm(float a, float b)
+{
+    return fminf(fmaxf(a, b), fmaxf(fminf(a, b), 0.0f));   // median(0, a, b)
+}
+#endif
 __device__ __forceinline__ f2 mm(f2 a, f2 b) { return f2{mm(a.x, b.x), mm(a.y, b.y)}; }
 
 // ---------------------------------------------------------------------------

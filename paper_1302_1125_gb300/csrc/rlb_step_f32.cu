@@ -17,10 +17,18 @@ static cudaError_t launch_f32(const StepParams &p, const float *f, const float *
     } else {
         // 32 x 8 threads (64 x 8 cells), two blocks per SM at <= 128 registers:
         // the best of a sweep over block shapes and register caps on GB300
-        block = dim3(32, 8, 1);
-        grid = dim3((npairs + 31) / 32, (p.ny + 7) / 8, p.nz);
+        block = dim3(32, RLB_F32_BY, 1);
+        grid = dim3((npairs + 31) / 32, (p.ny + RLB_F32_BY - 1) / RLB_F32_BY, p.nz);
     }
-    f32::step_f32_kernel<DIM, EULER, VEC2><<<grid, block, 0, s>>>(p, f, h, fo, ho, prev);
+    const size_t smem = f32::step_smem_bytes(int(block.x * block.y), f32::kStageOn && VEC2 && !EULER);
+    static bool attr_set = false;   // per instantiation
+    if (!attr_set) {
+        const cudaError_t e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    f32::step_f32_kernel<DIM, EULER, VEC2><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev);
     return cudaGetLastError();
 }
 

@@ -119,15 +119,34 @@ static __device__ __noinline__ float xval_mapped(const float *q, int idx0, int x
     return gh ? ghost : __ldg(q + idx0 + (c - x0));
 }
 
+// Where the stencil values of one population come from: straight from global
+// memory (GlobalSrc), or from this thread's shared-memory staging slots that
+// asynchronous copies filled earlier (StageSrc).  get(slot, off) returns the
+// pair at element offset `off` from idx0; `slot` is its staging slot: 0, 1, 2
+// for x0-2, x0, x0+2, then 3 + 3 (A - 1) + k for the k-th neighbour pair along
+// axis A (see stage_item).
+template <bool VEC2, int LD>
+struct GlobalSrc {
+    const float *q;
+    const Geo &g;
+    __device__ __forceinline__ f2 get(int, int off) const { return ldpair<VEC2, LD>(q, g, off); }
+};
+
+struct StageSrc {
+    const f2 *s;     // slot 0 of this thread's buffer
+    int stride;      // f2 elements between slots
+    __device__ __forceinline__ f2 get(int slot, int) const { return s[slot * stride]; }
+};
+
 // x0-2 .. x0+3 of one plane.  With even nx every thread loads three aligned
 // pairs; periodic edges wrap to aligned pairs, and the clamped (open) or ghost
 // (inlet) positions of the two edge columns are patched afterwards.
-template <bool VEC2, int LD>
-__device__ __forceinline__ void xstencil(const float *q, const Geo &g, const StepParams &p, float ghost,
-                                         float (&v)[6])
+template <bool VEC2, int LD, typename Src>
+__device__ __forceinline__ void xstencil(const Src &src, const float *q, const Geo &g, const StepParams &p,
+                                         float ghost, float (&v)[6])
 {
     if constexpr (VEC2) {
-        const f2 a = ld2<LD>(q + g.idx0 + g.oa), b = ld2<LD>(q + g.idx0), c = ld2<LD>(q + g.idx0 + g.oc);
+        const f2 a = src.get(0, g.oa), b = src.get(1, 0), c = src.get(2, g.oc);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
         if (g.xfix) {
             if (g.xfix & XF_LO_CLAMP) v[1] = v[0];
@@ -328,10 +347,11 @@ __device__ __forceinline__ float tau1(float P, float n, float eta_over_s)
 }
 
 // streaming increment of population I along axis A for the pair (+ bulk lap)
-template <bool IS_F, int I, int A, bool VEC2, int LD>
-__device__ __forceinline__ void axis2(const float *q, const Geo &g, const StepParams &p, const float (&xv)[6],
+template <bool IS_F, int I, int A, typename Src>
+__device__ __forceinline__ void axis2(const Src &src, const Geo &g, const StepParams &p, const float (&xv)[6],
                                       f2 C, float k1, float k2, float hl, f2 &inc, f2 &lap)
 {
+    constexpr int sb = 3 * A;   // first staging slot of axis A (A = 1, 2)
     constexpr int c = cdir<I, A>();
     constexpr bool need_lap = IS_F && I != 0;
     const float k = (c == 1 || c == -1) ? k1 : k2;
@@ -354,58 +374,160 @@ __device__ __forceinline__ void axis2(const float *q, const Geo &g, const StepPa
         }
     } else {
         if constexpr (c > 0) {
-            const f2 Aq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -2)), B = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -1));
-            const f2 Dq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 1));
+            const f2 Aq = src.get(sb, off_of<A>(g, p, -2)), B = src.get(sb + 1, off_of<A>(g, p, -1));
+            const f2 Dq = src.get(sb + 2, off_of<A>(g, p, 1));
             const f2 d0 = B - Aq, d1 = C - B, d2 = Dq - C;
             const f2 Dv = fma2(bc(hl), mm(d2, d1) - mm(d1, d0), d1);
             inc = fma2(bc(-k), Dv, inc);
             if constexpr (need_lap) lap = lap + (d2 - d1);
         } else if constexpr (c < 0) {
-            const f2 B = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 1));
-            const f2 Eq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 2));
+            const f2 B = src.get(sb, off_of<A>(g, p, -1)), Dq = src.get(sb + 1, off_of<A>(g, p, 1));
+            const f2 Eq = src.get(sb + 2, off_of<A>(g, p, 2));
             const f2 e0 = C - B, e1 = Dq - C, e2 = Eq - Dq;
             const f2 Dv = fma2(bc(-hl), mm(e1, e2) - mm(e0, e1), e1);
             inc = fma2(bc(k), Dv, inc);
             if constexpr (need_lap) lap = lap + (e1 - e0);
         } else if constexpr (need_lap) {
-            const f2 B = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, -1)), Dq = ldpair<VEC2, LD>(q, g, off_of<A>(g, p, 1));
+            const f2 B = src.get(sb, off_of<A>(g, p, -1)), Dq = src.get(sb + 1, off_of<A>(g, p, 1));
             lap = lap + ((Dq - C) - (C - B));
         }
     }
 }
 
 // f (or h) + streaming (+ bulk) of population I for the pair: the explicit part of Eq. 57
-template <int DIM, bool IS_F, int I, bool VEC2, int LD>
-__device__ __forceinline__ f2 streamed2(const float *q, const Geo &g, const StepParams &p, float ghost,
-                                        float k1, float k2, float hl, float kb)
+template <int DIM, bool IS_F, int I, bool VEC2, int LD, typename Src>
+__device__ __forceinline__ f2 streamed2(const Src &src, const float *q, const Geo &g, const StepParams &p,
+                                        float ghost, float k1, float k2, float hl, float kb)
 {
     constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
     float xv[6];
     f2 C;
     if constexpr (xneed) {
-        xstencil<VEC2, LD>(q, g, p, ghost, xv);
+        xstencil<VEC2, LD>(src, q, g, p, ghost, xv);
         C = mk(xv[2], xv[3]);
     } else {
-        C = ldpair<VEC2, LD>(q, g, 0);
+        C = src.get(1, 0);
     }
     f2 inc = bc(0.0f), lap = bc(0.0f);
-    if constexpr (xneed) axis2<IS_F, I, 0, VEC2, LD>(q, g, p, xv, C, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 1) axis2<IS_F, I, 1, VEC2, LD>(q, g, p, xv, C, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 2) axis2<IS_F, I, 2, VEC2, LD>(q, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (xneed) axis2<IS_F, I, 0>(src, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 1) axis2<IS_F, I, 1>(src, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 2) axis2<IS_F, I, 2>(src, g, p, xv, C, k1, k2, hl, inc, lap);
     if constexpr (IS_F && I != 0) inc = fma2(bc(kb), lap, inc);
     return C + inc;
+}
+
+// Asynchronous copies (cp.async, cached in L1) into shared memory, completed
+// per thread by cp.async.wait_group: no other thread reads the slots.
+__device__ __forceinline__ void cp8(unsigned dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+#ifndef RLB_STAGE_BUFS
+#define RLB_STAGE_BUFS 3
+#endif
+constexpr int kStageSlots = 9;   // pairs staged per population: 3 along x, 3 per other axis
+constexpr int kStageBufs = RLB_STAGE_BUFS;   // populations in flight: the one computed and the next ones
+constexpr int kStageAhead = kStageBufs - 1;  // prefetch distance in populations
+
+// Issue the copies of item J (J < 19: f population J, else h population
+// J - 19) into staging buffer J % kStageBufs: the same pairs, in the same
+// slots, that streamed2 reads through StageSrc.  dst0 = shared address of
+// slot 0 of buffer 0 of this thread, sstride = bytes between slots.
+template <int DIM, int J>
+__device__ __forceinline__ void stage_item(const float *f, const float *h, const Geo &g, const StepParams &p,
+                                           long long ps, unsigned dst0, unsigned sstride)
+{
+    constexpr bool IS_F = J < 19;
+    constexpr int I = IS_F ? J : J - 19;
+    constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
+    constexpr bool need_lap = IS_F && I != 0;
+    const float *q = (IS_F ? f : h) + I * ps + g.idx0;
+    const unsigned d = dst0 + unsigned(J % kStageBufs) * kStageSlots * sstride;
+    if constexpr (xneed) {
+        cp8(d + 0 * sstride, q + g.oa);
+        cp8(d + 2 * sstride, q + g.oc);
+    }
+    cp8(d + 1 * sstride, q);
+    auto axis = [&](auto ac) {
+        constexpr int A = decltype(ac)::value;
+        constexpr int c = cdir<I, A>();
+        const unsigned b = d + unsigned(3 * A) * sstride;
+        if constexpr (c > 0) {
+            cp8(b, q + off_of<A>(g, p, -2));
+            cp8(b + sstride, q + off_of<A>(g, p, -1));
+            cp8(b + 2 * sstride, q + off_of<A>(g, p, 1));
+        } else if constexpr (c < 0) {
+            cp8(b, q + off_of<A>(g, p, -1));
+            cp8(b + sstride, q + off_of<A>(g, p, 1));
+            cp8(b + 2 * sstride, q + off_of<A>(g, p, 2));
+        } else if constexpr (need_lap) {
+            cp8(b, q + off_of<A>(g, p, -1));
+            cp8(b + sstride, q + off_of<A>(g, p, 1));
+        }
+    };
+    if constexpr (DIM > 1) axis(std::integral_constant<int, 1>{});
+    if constexpr (DIM > 2) axis(std::integral_constant<int, 2>{});
+    cp_commit();
 }
 
 // The update of one pair of cells (Eq. 57 for f and h), shared by the grid
 // kernel and the batched tube kernel.  eos = eta/s and kb = the bulk
 // prefactor of the cell's grid or tube.
-template <int DIM, bool EULER, bool VEC2, int LD = LD_NC>
+//
+// park (PARK = true): this thread's slots in shared memory, slot k at
+// park[k * pstride]; the h-equilibrium coefficients wait there while the f
+// populations are updated, which frees their registers for the f loop.
+//
+// stage (STAGE = true, even nx, viscous step): the stencil of each population
+// is copied asynchronously into this thread's shared-memory slots
+// kStageAhead populations ahead of its use (stage_item), so that the loads of the next
+// populations are in flight while one is computed; stage = slot 0 of buffer
+// 0 of this thread, sstride = f2 elements between slots.
+template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false>
 __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
                                             const float *__restrict__ f, const float *__restrict__ h,
                                             float *__restrict__ fo, float *__restrict__ ho,
-                                            float *__restrict__ prev, long long ps)
+                                            float *__restrict__ prev, long long ps,
+                                            f2 *park = nullptr, int pstride = 0,
+                                            f2 *stage = nullptr, int sstride = 0)
 {
     const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim;
+    static_assert(!STAGE || (VEC2 && !EULER), "staging needs aligned pairs and the viscous step");
+    unsigned sdst0 = 0;
+    if constexpr (STAGE) {
+        sdst0 = unsigned(__cvta_generic_to_shared(stage));
+        for_pops(std::make_integer_sequence<int, kStageAhead>{}, [&](auto jc) {
+            stage_item<DIM, decltype(jc)::value>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
+        });
+    }
+    // the explicit part of item J (J < 19: f population J, else h population J - 19)
+    auto item = [&](auto jc) -> f2 {
+        constexpr int J = decltype(jc)::value;
+        constexpr bool IS_F = J < 19;
+        constexpr int I = IS_F ? J : J - 19;
+        const float *q = (IS_F ? f : h) + I * ps;
+        const float ghost = IS_F ? p.f_ghost_f[I] : p.f_ghost_h[I];
+        if constexpr (STAGE) {
+            if constexpr (J + kStageAhead < 38) {
+                stage_item<DIM, J + kStageAhead>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
+                cp_wait<kStageAhead>();
+            } else {
+                cp_wait<37 - J>();   // the groups issued after item J's
+            }
+            const StageSrc src{stage + (J % kStageBufs) * kStageSlots * sstride, sstride};
+            return streamed2<DIM, IS_F, I, VEC2, LD>(src, q, g, p, ghost, k1, k2, hl, kb);
+        } else {
+            const GlobalSrc<VEC2, LD> src{q, g};
+            return streamed2<DIM, IS_F, I, VEC2, LD>(src, q, g, p, ghost, k1, k2, hl, kb);
+        }
+    };
 
     if constexpr (!EULER) {
         // raw sums of the local populations: S = sum f, V_a = sum c_a f
@@ -454,6 +576,22 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         Ta[1] = fma2(bc(2.0f), Vy.hi + Vy.lo, -Vpy);
         Ta[2] = fma2(bc(2.0f), Vz.hi + Vz.lo, -Vpz);
 
+        // h coefficients of 2 h^eq(t) - h^eq(t - dt) (Eq. 58) and their N^0
+        // target, formed now so that mt and mp die before the f loop
+        f2 H0, Hb[3], Hd[3], Ho[3];
+        {
+            f2 L0, Lb[3], Ld[3], Lo[3];
+            coef_h2(mt, H0, Hb, Hd, Ho);
+            coef_h2(mp, L0, Lb, Ld, Lo);
+            H0 = fma2(bc(2.0f), H0, -L0);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                Hb[j] = fma2(bc(2.0f), Hb[j], -Lb[j]);
+                Hd[j] = fma2(bc(2.0f), Hd[j], -Ld[j]);
+                Ho[j] = fma2(bc(2.0f), Ho[j], -Lo[j]);
+            }
+        }
+        f2 T0h = fma2(bc(2.0f), Sh, -Shp);
         {
             f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
             coef_f2(mt, K0, Kb, Kd, Ko);
@@ -466,48 +604,58 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                 Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
             }
             const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), T0, Ta);
+            // the raw sums of this level become the next step's previous level
+            stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
+            stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
+            stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
+            stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
+            stpair<VEC2>(prev + 4 * ps, g, Sh);
+            if constexpr (PARK) {
+                park[0] = H0;
+                park[10 * pstride] = T0h;
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    park[(1 + j) * pstride] = Hb[j];
+                    park[(4 + j) * pstride] = Hd[j];
+                    park[(7 + j) * pstride] = Ho[j];
+                }
+            }
             for_pops(RLB_F32_POPS, [&](auto ic) {
                 constexpr int I = decltype(ic)::value;
-                const f2 pre = streamed2<DIM, true, I, VEC2, LD>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
+                const f2 pre = item(std::integral_constant<int, I>{});
                 stpair<VEC2>(fo + I * ps, g, fma2(kap, eq2<I>(ef) - pre, pre));
             });
         }
         {
-            const f2 T0h = fma2(bc(2.0f), Sh, -Shp);
-            f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
-            coef_h2(mt, K0, Kb, Kd, Ko);
-            coef_h2(mp, L0, Lb, Ld, Lo);
-            K0 = fma2(bc(2.0f), K0, -L0);
+            if constexpr (PARK) {
+                H0 = park[0];
+                T0h = park[10 * pstride];
 #pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                Kb[j] = fma2(bc(2.0f), Kb[j], -Lb[j]);
-                Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
-                Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
+                for (int j = 0; j < 3; ++j) {
+                    Hb[j] = park[(1 + j) * pstride];
+                    Hd[j] = park[(4 + j) * pstride];
+                    Ho[j] = park[(7 + j) * pstride];
+                }
             }
-            const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
+            const W2 eh = weigh2(H0, Hb, Hd, Ho, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
             for_pops(RLB_F32_POPS, [&](auto ic) {
                 constexpr int I = decltype(ic)::value;
-                const f2 pre = streamed2<DIM, false, I, VEC2, LD>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb);
+                const f2 pre = item(std::integral_constant<int, 19 + I>{});
                 stpair<VEC2>(ho + I * ps, g, fma2(kap, eq2<I>(eh) - pre, pre));
             });
         }
-        stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
-        stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
-        stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
-        stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
-        stpair<VEC2>(prev + 4 * ps, g, Sh);
     } else {
         // Euler mode (Sec. III): f, h <- equilibria of the streamed state
         df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
         for_pops(RLB_F32_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            const f2 v = streamed2<DIM, true, I, VEC2, LD>(f + I * ps, g, p, p.f_ghost_f[I], k1, k2, hl, kb);
+            const f2 v = item(std::integral_constant<int, I>{});
             acc(S, v);
             constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
             if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
             if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
             if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
-            acc(Hs, streamed2<DIM, false, I, VEC2, LD>(h + I * ps, g, p, p.f_ghost_h[I], k1, k2, hl, kb));
+            acc(Hs, item(std::integral_constant<int, 19 + I>{}));
         });
         const f2 Sh = Hs.hi + Hs.lo;
         bool ok0, ok1;
@@ -532,11 +680,35 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
     }
 }
 
-template <int DIM, bool EULER, bool VEC2>
-__global__ void __launch_bounds__(256, VEC2 ? 2 : 1) step_f32_kernel(const StepParams p, const float *__restrict__ f,
-                                                       const float *__restrict__ h, float *__restrict__ fo,
-                                                       float *__restrict__ ho, float *__restrict__ prev)
+#ifndef RLB_F32_MINB
+#define RLB_F32_MINB 2
+#endif
+#ifndef RLB_F32_BY
+#define RLB_F32_BY 8
+#endif
+constexpr int kParkSlots = 11;   // f2 slots per thread in shared memory
+#ifdef RLB_NO_PARK
+constexpr bool kParkOn = false;
+#else
+constexpr bool kParkOn = true;
+#endif
+#ifdef RLB_NO_STAGE
+constexpr bool kStageOn = false;
+#else
+constexpr bool kStageOn = true;
+#endif
+// dynamic shared memory of one block of nthr threads
+constexpr size_t step_smem_bytes(int nthr, bool stage)
 {
+    return sizeof(f2) * size_t(nthr) * ((kParkOn ? kParkSlots : 0) + (stage ? kStageSlots * kStageBufs : 0));
+}
+
+template <int DIM, bool EULER, bool VEC2>
+__global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
+    step_f32_kernel(const StepParams p, const float *__restrict__ f, const float *__restrict__ h,
+                    float *__restrict__ fo, float *__restrict__ ho, float *__restrict__ prev)
+{
+    extern __shared__ f2 s_park[];
     const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     const int z = blockIdx.z;
@@ -570,7 +742,12 @@ __global__ void __launch_bounds__(256, VEC2 ? 2 : 1) step_f32_kernel(const StepP
             g.zoff[k] = DIM > 2 ? (map1(z + ds[k], p.nz, p.bc_lo[2], p.bc_hi[2], gh) - z) * p.nx * p.ny : 0;
         }
     }
-    update_pair<DIM, EULER, VEC2>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho, prev, ps);
+    const int nthr = blockDim.x * blockDim.y;
+    const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+    constexpr bool STAGE = kStageOn && VEC2 && !EULER;
+    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho, prev, ps,
+                                                         s_park + tid, nthr,
+                                                         s_park + (kParkOn ? kParkSlots * nthr : 0) + tid, nthr);
 }
 
 }  // namespace f32
