@@ -68,6 +68,8 @@ __device__ __forceinline__ f32::Geo tube_geo(int off, int nx, int x0)
 
 // LD = f32::LD_CA for C = 1 (only this block writes the job's tubes),
 // f32::LD_CG for C > 1 (the other blocks of the cluster write them too).
+// The stencils are staged through shared memory by cp.async (see
+// update_pair).
 // MAXT = launch bound: 512 caps the kernel at 128 registers (some spill),
 // 384 at 168, 256 leaves it unconstrained; the autotuner picks.
 template <int LD, int MAXT>
@@ -76,6 +78,7 @@ __global__ void __launch_bounds__(MAXT, 1) tubes_kernel(const Args a)
     __shared__ int s_off[kMaxJobTubes], s_nx[kMaxJobTubes], s_steps[kMaxJobTubes], s_par[kMaxJobTubes];
     __shared__ int s_tube[kMaxJobTubes], s_p0[kMaxJobTubes + 1];
     __shared__ float s_eos[kMaxJobTubes], s_kb[kMaxJobTubes];
+    extern __shared__ f2 s_dyn[];   // parked coefficients and staged stencils (see update_pair)
 
     const int C = a.cluster;
     const unsigned rank = C > 1 ? cluster_rank() : 0u;
@@ -118,7 +121,10 @@ __global__ void __launch_bounds__(MAXT, 1) tubes_kernel(const Args a)
                     const bool odd = ((s_par[i] + s) & 1) != 0;
                     const float *f = odd ? a.f1 : a.f0, *h = odd ? a.h1 : a.h0;
                     float *fo = odd ? a.f0 : a.f1, *ho = odd ? a.h0 : a.h1;
-                    f32::update_pair<1, false, true, LD>(a.p, g, s_eos[i], s_kb[i], f, h, fo, ho, a.prev, a.ps);
+                    f32::update_pair<1, false, true, LD, f32::kParkOn, f32::kStageOn>(
+                        a.p, g, s_eos[i], s_kb[i], f, h, fo, ho, a.prev, a.ps, s_dyn + threadIdx.x,
+                        int(blockDim.x), s_dyn + (f32::kParkOn ? f32::kParkSlots * blockDim.x : 0) + threadIdx.x,
+                        int(blockDim.x));
                 }
             }
             if (C > 1) cluster_barrier();
@@ -136,7 +142,12 @@ cudaError_t launch_variant(const Args &a, int threads, int cluster, cudaStream_t
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nclusters_out ? unsigned(cluster) : unsigned(a.nclusters * cluster), 1, 1);
     cfg.blockDim = dim3(unsigned(threads), 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    const size_t smem = f32::step_smem_bytes(threads, f32::kStageOn, 1);
+    cfg.dynamicSmemBytes = smem;
+    if (smem > 48 * 1024) {
+        const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+        if (e != cudaSuccess) return e;
+    }
     cfg.stream = s;
     cudaLaunchAttribute at[1];
     if (cluster > 1) {
@@ -150,7 +161,7 @@ cudaError_t launch_variant(const Args &a, int threads, int cluster, cudaStream_t
     if (nclusters_out) {
         if (cluster > 1) return cudaOccupancyMaxActiveClusters(nclusters_out, kern, &cfg);
         int per_sm = 0, dev = 0, sms = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         *nclusters_out = per_sm * sms;

@@ -20,7 +20,7 @@ static cudaError_t launch_f32(const StepParams &p, const float *f, const float *
         block = dim3(32, RLB_F32_BY, 1);
         grid = dim3((npairs + 31) / 32, (p.ny + RLB_F32_BY - 1) / RLB_F32_BY, p.nz);
     }
-    const size_t smem = f32::step_smem_bytes(int(block.x * block.y), f32::kStageOn && VEC2 && !EULER);
+    const size_t smem = f32::step_smem_bytes(int(block.x * block.y), f32::kStageOn && VEC2 && !EULER, DIM);
     static bool attr_set = false;   // per instantiation
     if (!attr_set) {
         const cudaError_t e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2>,

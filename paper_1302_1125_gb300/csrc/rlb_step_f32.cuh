@@ -432,7 +432,12 @@ __device__ __forceinline__ void cp_wait()
 #ifndef RLB_STAGE_BUFS
 #define RLB_STAGE_BUFS 3
 #endif
-constexpr int kStageSlots = 9;   // pairs staged per population: 3 along x, 3 per other axis
+// pairs staged per population: 3 along x, 3 along each other streamed axis
+template <int DIM>
+constexpr int stage_slots()
+{
+    return 3 * DIM;
+}
 constexpr int kStageBufs = RLB_STAGE_BUFS;   // populations in flight: the one computed and the next ones
 constexpr int kStageAhead = kStageBufs - 1;  // prefetch distance in populations
 
@@ -449,7 +454,7 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
     constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
     constexpr bool need_lap = IS_F && I != 0;
     const float *q = (IS_F ? f : h) + I * ps + g.idx0;
-    const unsigned d = dst0 + unsigned(J % kStageBufs) * kStageSlots * sstride;
+    const unsigned d = dst0 + unsigned(J % kStageBufs) * stage_slots<DIM>() * sstride;
     if constexpr (xneed) {
         cp8(d + 0 * sstride, q + g.oa);
         cp8(d + 2 * sstride, q + g.oc);
@@ -521,7 +526,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
             } else {
                 cp_wait<37 - J>();   // the groups issued after item J's
             }
-            const StageSrc src{stage + (J % kStageBufs) * kStageSlots * sstride, sstride};
+            const StageSrc src{stage + (J % kStageBufs) * stage_slots<DIM>() * sstride, sstride};
             return streamed2<DIM, IS_F, I, VEC2, LD>(src, q, g, p, ghost, k1, k2, hl, kb);
         } else {
             const GlobalSrc<VEC2, LD> src{q, g};
@@ -698,9 +703,9 @@ constexpr bool kStageOn = false;
 constexpr bool kStageOn = true;
 #endif
 // dynamic shared memory of one block of nthr threads
-constexpr size_t step_smem_bytes(int nthr, bool stage)
+constexpr size_t step_smem_bytes(int nthr, bool stage, int dim)
 {
-    return sizeof(f2) * size_t(nthr) * ((kParkOn ? kParkSlots : 0) + (stage ? kStageSlots * kStageBufs : 0));
+    return sizeof(f2) * size_t(nthr) * ((kParkOn ? kParkSlots : 0) + (stage ? 3 * dim * kStageBufs : 0));
 }
 
 template <int DIM, bool EULER, bool VEC2>
