@@ -86,6 +86,8 @@ def lib():
         _lib.orc_step_cells.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_void_p, C.c_void_p,
                                         C.c_int, C.c_long, C.POINTER(C.c_long), dp, dp, dp]
         _lib.orc_step_cells.restype = C.c_long
+        _lib.orc_solid_reset.argtypes = [C.POINTER(_Params), C.c_void_p, C.c_double, C.c_double, dp, dp, dp]
+        _lib.orc_solid_reset.restype = None
         _lib.orc_macroscopic.argtypes = [C.POINTER(_Params), dp, dp, dp]
         _lib.orc_macroscopic.restype = C.c_long
         _lib.orc_nu.restype = C.c_double
@@ -214,6 +216,7 @@ class State:
     h: np.ndarray = field(repr=False)
     prev: np.ndarray = field(repr=False)
     nonphysical: int = 0
+    solid: tuple = None     # (mask uint8[N], n, T): cells held at equilibrium
 
 
 def init(p: Params, n, T, ux, uy, uz) -> State:
@@ -236,6 +239,24 @@ def step(s: State, nsteps: int = 1) -> State:
         s.nonphysical += lib().orc_step(C.byref(cp), _p(s.f), _p(s.h), _p(s.prev), _p(fo), _p(ho))
         s.f, fo = fo, s.f
         s.h, ho = ho, s.h
+        if s.solid is not None:
+            _solid_reset(s)
+    return s
+
+
+def _solid_reset(s: State):
+    mask, n, T = s.solid
+    cp = s.p.c()
+    lib().orc_solid_reset(C.byref(cp), mask.ctypes.data, float(n), float(T), _p(s.f), _p(s.h), _p(s.prev))
+
+
+def set_solid(s: State, mask, n: float, T: float) -> State:
+    """Hold the cells where mask != 0 at the equilibrium of (n, T, u = 0):
+    applied now and after every step (orc_solid_reset)."""
+    m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, np.uint8)
+    assert m.size == s.p.N
+    s.solid = (m, float(n), float(T))
+    _solid_reset(s)
     return s
 
 

@@ -505,6 +505,30 @@ void orc_init(const orc_params *p, const double *n, const double *T,
     }
 }
 
+void orc_solid_reset(const orc_params *p, const unsigned char *mask, double n, double T,
+                     double *f, double *h, double *prev)
+{
+    const long N = (long)p->g.nx * p->g.ny * p->g.nz;
+    const double rest[3] = {0.0, 0.0, 0.0};
+    double fe[19], he[19];
+    long idx;
+    int i;
+    orc_feq(n * T, rest, fe);
+    orc_heq(n, rest, he);
+    for (idx = 0; idx < N; ++idx) {
+        if (!mask[idx]) continue;
+        for (i = 0; i < 19; ++i) {
+            f[(long)i * N + idx] = fe[i];
+            h[(long)i * N + idx] = he[i];
+        }
+        prev[0 * N + idx] = n * T;
+        prev[1 * N + idx] = 0.0;
+        prev[2 * N + idx] = 0.0;
+        prev[3 * N + idx] = 0.0;
+        prev[4 * N + idx] = n;
+    }
+}
+
 long orc_step(const orc_params *p, const double *f, const double *h,
               double *prev, double *fout, double *hout)
 {

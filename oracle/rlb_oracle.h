@@ -88,6 +88,13 @@ long orc_step_cells(const orc_params *p, const void *f, const void *h,
                     double *fout, double *hout, double *mout);
 long orc_macroscopic(const orc_params *p, const double *f, const double *h,
                      double *out);
+/* solid cells (Sec. III, the astrophysical run: a fixed cloud whose cells
+ * evolve to the equilibrium of the constant state n, T, u = 0): every cell
+ * with mask[idx] != 0 is set to f^eq(P = n T, 0), h^eq(n, 0) with the
+ * previous level (P, 0, 0, 0, n).  The time loop applies it after every
+ * step (reading R11). */
+void orc_solid_reset(const orc_params *p, const unsigned char *mask, double n, double T,
+                     double *f, double *h, double *prev);
 
 #ifdef __cplusplus
 }

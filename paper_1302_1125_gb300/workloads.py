@@ -44,6 +44,16 @@ used instead:
                 membrane at Nx/2, alpha 0.2, dt/dx 0.15, 4 Nx steps each.
                 (Left slabs moving faster than gamma ~ 1.5 into gas at rest
                 are non-physical after one step, as for tube_8192.)
+  sphere_cloud  the paper's 3-D astrophysical run: 200 x 100 x 100 cells, a
+                slab x <= 65 at (n0, T0) and ambient (n1, T1) = (n_eq(1), 1) at
+                rest, a solid sphere of radius 10 at (100, 50, 50) held at
+                (n1, T1, u = 0), the inlet at x = 0 holding (n0, T0), open
+                faces elsewhere; case "beta02": T0 = 2.71 T1, n0 = 0.9 n1;
+                case "beta09": T0 = 54.77 T1, n0 = 10.95 n1; inviscid (Euler
+                mode) or viscous with tau = 1; alpha 0.2, dt/dx 0.15, 1000
+                steps.  (The printed setup puts (n1, T1) on the slab side but
+                fixes the inlet there at (n0, T0) and the cloud, held at
+                (n1, T1), on the other side: read as slab = (n0, T0).)
 """
 from __future__ import annotations
 
@@ -80,6 +90,7 @@ class Workload:
     alpha_override: float = -1.0
     euler_mode: int = 0
     make_fields: object = field(default=None, repr=False)
+    solid: tuple = None     # (make_mask -> uint8[N], n, T): cells held at equilibrium (n, T, u = 0)
 
     @property
     def N(self) -> int:
@@ -88,6 +99,10 @@ class Workload:
     def fields(self):
         """(n, T, ux, uy, uz), float64 arrays of N values, x fastest."""
         return self.make_fields()
+
+    def solid_mask(self):
+        """uint8[N] mask of the solid cells (None without solid cells)."""
+        return None if self.solid is None else self.solid[0]()
 
 
 def _tube_fields(nx, ny, nz, left, right, x0=None):
@@ -262,3 +277,36 @@ def periodic_box(nx, ny=1, nz=1, *, seed=7, amp=0.2, gamma_max=3.0, dt_over_dx=0
     return Workload(name, nx, ny, nz, per, per, dt_over_dx, 0.1, 0.0, steps, precision,
                     tau_override=tau_override, alpha_override=alpha_override,
                     make_fields=lambda: tuple(a.copy() for a in fl))
+
+
+def sphere_cloud(case="beta09", scale=1, *, viscous=False, precision=FP32_STORAGE, steps=None) -> Workload:
+    """The paper's 3-D shock-cloud run with a solid sphere (Sec. III), every
+    length divided by `scale` (steps too, so the same physical time)."""
+    T0, r = {"beta02": (2.71, 0.9), "beta09": (54.77, 10.95)}[case]
+    nx, ny, nz = 200 // scale, 100 // scale, 100 // scale
+    T1 = 1.0
+    n1 = float(n_eq(T1))
+    n0 = r * n1
+    xs = 65.0 / scale
+    cx, cy, cz, R = 100.0 / scale, 50.0 / scale, 50.0 / scale, 10.0 / scale
+
+    def make():
+        x = np.arange(nx, dtype=np.float64)
+        slab = np.broadcast_to(x <= xs, (nz, ny, nx)).reshape(-1)
+        n = np.where(slab, n0, n1).astype(np.float64)
+        T = np.where(slab, T0, T1).astype(np.float64)
+        z = np.zeros_like(n)
+        return n, T, z, z.copy(), z.copy()
+
+    def mask():
+        zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+        d2 = (xx - cx) ** 2 + (yy - cy) ** 2 + (zz - cz) ** 2
+        return np.ascontiguousarray((d2 <= R * R).reshape(-1), np.uint8)
+
+    out = (BC_OUTFLOW, BC_OUTFLOW, BC_OUTFLOW)
+    return Workload(f"sphere_cloud_{case}" + ("_viscous" if viscous else "") + (f"_s{scale}" if scale > 1 else ""),
+                    nx, ny, nz, (BC_INLET, BC_OUTFLOW, BC_OUTFLOW), out, 0.15, 0.0, 0.0,
+                    steps if steps is not None else 1000 // scale, precision,
+                    inlet=(n0, T0, (0.0, 0.0, 0.0)), tau_override=1.0 if viscous else 0.0,
+                    alpha_override=0.2, euler_mode=0 if viscous else 1, make_fields=make,
+                    solid=(mask, n1, T1))

@@ -8,7 +8,9 @@ the printed one-cell-downstream flux difference of Eq. 47, a doubled
 off-diagonal equilibrium coefficient, a sign in Eq. 58, lambda_0 != 0 in
 Eq. 55, a dropped nu in the collision prefactor of Eq. 57, the wrong sign of
 the extrapolated equilibrium, n = N^0 gamma, a flipped lattice vector, tau
-without nu^2 (Eq. 41), minmod taking the larger slope (Eq. 53).
+without nu^2 (Eq. 41), minmod taking the larger slope (Eq. 53), and in the
+solid cells of the astrophysical run (Sec. III): no reset, a moving or a
+wrong-pressure cloud state.
 """
 import os
 import subprocess
@@ -19,7 +21,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "rlb_oracle.c")
 PINS = ["tests/test_oracle_lattice.py", "tests/test_oracle_equilibrium.py",
-        "tests/test_oracle_stream.py", "tests/test_oracle_step.py"]
+        "tests/test_oracle_stream.py", "tests/test_oracle_step.py", "tests/test_oracle_solid.py"]
 
 MUTATIONS = {
     "printed_delta_plus_in_fR": ("fR -= 0.5 * orc_minmod(dm_y, dm_yp1);",
@@ -42,6 +44,9 @@ MUTATIONS = {
                                "L.c[i][b] = (i == 12 ? -2.0 : 2.0) * ca * s2;"),
     "tau_without_nu_squared": ("return 0.5 + NU * NU * eta / (4.0 * P);",
                                "return 0.5 + eta / (4.0 * P);"),
+    "solid_reset_skipped": ("if (!mask[idx]) continue;", "if (mask[idx] || !mask[idx]) continue;"),
+    "solid_state_moving": ("const double rest[3] = {0.0, 0.0, 0.0};", "const double rest[3] = {0.05, 0.0, 0.0};"),
+    "solid_pressure_without_T": ("orc_feq(n * T, rest, fe);", "orc_feq(n, rest, fe);"),
     "minmod_takes_larger_slope": ("return 0.5 * fmin(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));",
                                   "return 0.5 * fmax(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));"),
 }
