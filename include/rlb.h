@@ -127,11 +127,25 @@ RLB_API rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, do
 RLB_API rlb_status rlb_init(rlb_ctx *ctx, const double *n, const double *T, const double *ux,
                     const double *uy, const double *uz, int on_device);
 
-/* Advance nsteps time steps of Eq. 57 (nsteps >= 0).  Kernels are queued on
- * the context's stream; the call then waits for them and returns
+/* Advance nsteps time steps of Eq. 57 (nsteps >= 0): one step-kernel launch
+ * per step (plus one solid-cell reset launch per step when rlb_set_solid
+ * holds cells).  Kernels are queued on the context's stream; the call then
+ * waits for them and returns
  * RLB_E_NONPHYSICAL if any cell of any step was non-physical (the status word
  * is then cleared). */
 RLB_API rlb_status rlb_step(rlb_ctx *ctx, long long nsteps);
+
+/* Solid cells (Sec. III, the astrophysical run: a fixed cloud whose cells
+ * evolve to the equilibrium of the constant state n1, T1, u = 0).  Every
+ * cell with mask[idx] != 0 (mask: N bytes, host or device memory per
+ * on_device) is set to f^eq(P = n T, u = 0), h^eq(n, u = 0) and the previous
+ * level of that state, now and after every later step, in a separate kernel
+ * over the solid cells' index list (the step kernel itself is unchanged).
+ * A call replaces the previous set; mask = NULL removes it.  RLB_E_INVALID
+ * for n <= 0 or T <= 0; RLB_E_NOMEM if the index list cannot be allocated.
+ * Synchronous. */
+RLB_API rlb_status rlb_set_solid(rlb_ctx *ctx, const unsigned char *mask, double n, double T,
+                                 int on_device);
 
 /* Macroscopic fields of the current populations (Sec. II: moments and the
  * Landau-frame recovery): out holds 6 N doubles, planes n, e, u_x, u_y, u_z,

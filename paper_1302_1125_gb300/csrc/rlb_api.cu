@@ -9,6 +9,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <vector>
 
 #include "../../include/rlb.h"
 #include "rlb_device.cuh"
@@ -34,6 +35,8 @@ struct rlb_ctx {
     unsigned *h_status;   // pinned
     double *h_tot;        // pinned
     int cur;
+    int nsolid;           // solid cells (rlb_set_solid)
+    void *solid;          // device: 3 doubles {n, T, 0}, then nsolid cell indices
     cudaStream_t stream;
     long long launches;
     StepParams sp;
@@ -347,8 +350,54 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
         if (e != cudaSuccess) return cuda_fail(ctx, e, "step kernel launch");
         ctx->launches += 1;
         ctx->cur = o;
+        if (ctx->nsolid > 0) {
+            RLB_CUDA(ctx, rlb::launch_solid_reset(ctx->fp32, ctx->nsolid, (const int *)((double *)ctx->solid + 3),
+                                                  ctx->ps, (const double *)ctx->solid, ctx->fbuf[o], ctx->hbuf[o],
+                                                  ctx->prev, ctx->d_status, ctx->stream));
+            ctx->launches += 1;
+        }
     }
     return check_device_status(ctx, RLB_E_NONPHYSICAL);
+}
+
+rlb_status rlb_set_solid(rlb_ctx *ctx, const unsigned char *mask, double n, double T, int on_device)
+{
+    if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
+    RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->solid) cudaFree(ctx->solid);
+    ctx->solid = nullptr;
+    ctx->nsolid = 0;
+    if (!mask) return RLB_OK;
+    if (!(n > 0.0) || !(T > 0.0) || !std::isfinite(n * T))
+        return fail(ctx, RLB_E_INVALID, "the solid state needs n > 0 and T > 0");
+    std::vector<unsigned char> hm;
+    const unsigned char *m = mask;
+    if (on_device) {
+        hm.resize((size_t)ctx->N);
+        RLB_CUDA(ctx, cudaMemcpy(hm.data(), mask, (size_t)ctx->N, cudaMemcpyDeviceToHost));
+        m = hm.data();
+    }
+    std::vector<int> idx;
+    for (int i = 0; i < ctx->N; ++i)
+        if (m[i]) idx.push_back(i);
+    if (idx.empty()) return RLB_OK;
+    const size_t bytes = 3 * sizeof(double) + sizeof(int) * idx.size();
+    cudaError_t e = cudaMalloc(&ctx->solid, bytes);
+    if (e != cudaSuccess) {
+        ctx->solid = nullptr;
+        return fail(ctx, RLB_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    const double st[3] = {n, T, 0.0};
+    RLB_CUDA(ctx, cudaMemcpy(ctx->solid, st, sizeof(st), cudaMemcpyHostToDevice));
+    RLB_CUDA(ctx, cudaMemcpy((double *)ctx->solid + 3, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice));
+    ctx->nsolid = int(idx.size());
+    const int c = ctx->cur;
+    RLB_CUDA(ctx, rlb::launch_solid_reset(ctx->fp32, ctx->nsolid, (const int *)((double *)ctx->solid + 3), ctx->ps,
+                                          (const double *)ctx->solid, ctx->fbuf[c], ctx->hbuf[c], ctx->prev,
+                                          ctx->d_status, ctx->stream));
+    ctx->launches += 1;
+    return check_device_status(ctx, RLB_E_INVALID);
 }
 
 rlb_status rlb_macroscopic(rlb_ctx *ctx, double *out, int on_device)
@@ -442,6 +491,7 @@ void rlb_destroy(rlb_ctx *ctx)
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     else cudaDeviceSynchronize();
     if (ctx->block) cudaFree(ctx->block);
+    if (ctx->solid) cudaFree(ctx->solid);
     if (ctx->h_status) cudaFreeHost(ctx->h_status);
     delete ctx;
 }

@@ -26,6 +26,17 @@ __global__ void macro_kernel(int N, long long ps, const T *__restrict__ f,
     macro_cell<T>(idx, ps, f, h, out, idx, N, status);
 }
 
+// solid cells: the equilibrium of st = {n, T, 0} (the same code as the
+// initialisation, so a solid cell holds what rlb_init writes for that state)
+template <typename T>
+__global__ void solid_reset_kernel(int M, const int *__restrict__ idx, long long ps, const double *__restrict__ st,
+                                   T *__restrict__ f, T *__restrict__ h, T *__restrict__ prev, unsigned *status)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= M) return;
+    init_cell<T>(0, idx[j], ps, st, st + 1, st + 2, st + 2, st + 2, f, h, prev, status);
+}
+
 // per-block partial sums of (T^00, T^0x, T^0y, T^0z, N^0); fixed grid and
 // fixed reduction order, so the result is deterministic
 constexpr int kTotBlock = 256;
@@ -97,6 +108,18 @@ cudaError_t launch_macro(int fp32, int N, long long ps, const void *f, const voi
     else
         macro_kernel<double><<<g, b, 0, s>>>(N, ps, (const double *)f, (const double *)h, out,
                                              status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solid_reset(int fp32, int M, const int *idx, long long ps, const double *st, void *f,
+                               void *h, void *prev, unsigned *status, cudaStream_t s)
+{
+    const int b = 128, g = (M + b - 1) / b;
+    if (fp32)
+        solid_reset_kernel<float><<<g, b, 0, s>>>(M, idx, ps, st, (float *)f, (float *)h, (float *)prev, status);
+    else
+        solid_reset_kernel<double><<<g, b, 0, s>>>(M, idx, ps, st, (double *)f, (double *)h, (double *)prev,
+                                                   status);
     return cudaGetLastError();
 }
 

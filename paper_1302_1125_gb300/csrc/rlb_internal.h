@@ -40,6 +40,11 @@ int totals_blocks(int N);
 cudaError_t launch_totals(int fp32, int N, long long ps, const void *f, const void *h,
                           double *partial, double *out, cudaStream_t s);
 
+// solid cells: the M cells idx[0..M) are set to the equilibrium of the
+// state st = {n, T, 0} (device doubles) in f, h and the previous level
+cudaError_t launch_solid_reset(int fp32, int M, const int *idx, long long ps, const double *st, void *f,
+                               void *h, void *prev, unsigned *status, cudaStream_t s);
+
 // set the text rlb_last_error(NULL) returns on this thread
 void set_thread_error(const char *msg);
 

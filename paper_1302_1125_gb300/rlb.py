@@ -96,6 +96,8 @@ def lib() -> C.CDLL:
         L.rlb_last_error.restype = C.c_char_p
         L.rlb_status_string.argtypes = [C.c_int]
         L.rlb_status_string.restype = C.c_char_p
+        L.rlb_set_solid.argtypes = [ctxp, vp, C.c_double, C.c_double, C.c_int]
+        L.rlb_set_solid.restype = C.c_int
         L.rlb_conserved_totals_noalloc.argtypes = [vp, vp, C.c_int, C.c_longlong, C.c_int, vp, vp]
         L.rlb_conserved_totals_noalloc.restype = C.c_int
         ip, llp, tp = C.POINTER(C.c_int), C.POINTER(C.c_longlong), C.POINTER(rlb_batch_tuning)
@@ -292,6 +294,23 @@ class Grid:
 
     def step(self, nsteps=1):
         rlb_step(self.ctx, nsteps)
+        return self
+
+    def set_solid(self, mask, n, T):
+        """hold the cells where mask != 0 at the equilibrium of (n, T, u = 0)
+        (mask: N values, numpy or torch CUDA; None removes the solid cells)"""
+        if mask is None:
+            _check(lib().rlb_set_solid(self.ctx, None, 1.0, 1.0, 0), self.ctx)
+            return self
+        if hasattr(mask, "is_cuda") and mask.is_cuda:
+            torch = _torch()
+            m = (mask.reshape(-1) != 0).to(torch.uint8).contiguous()
+            _check(lib().rlb_set_solid(self.ctx, m.data_ptr(), float(n), float(T), 1), self.ctx)
+        else:
+            m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, np.uint8)
+            if m.size != self.N:
+                raise ValueError(f"mask has {m.size} values, expected {self.N}")
+            _check(lib().rlb_set_solid(self.ctx, m.ctypes.data, float(n), float(T), 0), self.ctx)
         return self
 
     def macroscopic(self, device=True):
