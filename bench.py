@@ -323,6 +323,38 @@ def batch_sweep(torch, rlb, W, hbm_peak, device_index):
             "clocks": clk}
 
 
+def sphere_run(torch, rlb, W, device_index):
+    """The paper's own 3-D run (Sec. III): 200 x 100 x 100 cells with a solid
+    sphere held at the ambient equilibrium, beta ~ 0.2 shock, viscous
+    (tau = 1); FP32 storage for all 1000 steps, FP64 for 100."""
+    w = W.sphere_cloud("beta02", viscous=True)
+    fields = [torch.as_tensor(a, device="cuda") for a in w.fields()]
+    out = {"workload": "sphere_cloud: the paper's 3-D shock-cloud run, 200x100x100, solid sphere r=10 at "
+                       "(100,50,50) held at (n1, T1, u=0), slab x<=65 at T0=2.71 T1, n0=0.9 n1, inlet at x=0, "
+                       "open faces, tau=1, alpha 0.2, dt/dx 0.15",
+           "cells": w.N, "solid_cells": int(w.solid_mask().sum()), "unit": UNIT}
+    stream = torch.cuda.current_stream()
+    for name, prec, steps in (("fp32_storage", rlb.FP32_STORAGE, w.steps), ("fp64", rlb.FP64, 100)):
+        g = rlb.Grid.from_workload(w, precision=prec)
+        g.init(*fields)
+        g.set_solid(w.solid_mask(), w.solid[1], w.solid[2])
+        g.step(3)
+        g.init(*fields)
+        g.set_solid(w.solid_mask(), w.solid[1], w.solid[2])
+        torch.cuda.synchronize()
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = g.launches
+        s0.record(stream)
+        g.step(steps)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        ms = s0.elapsed_time(s1)
+        out[name] = {"value": w.N * steps / (ms * 1e-3) / 1e6, "steps": steps, "ms_per_step": ms / steps,
+                     "gpu_launches": g.launches - l0}
+        g.close()
+    return out
+
+
 def run_ours(args):
     global _dist
     import torch
@@ -389,6 +421,7 @@ def run_ours(args):
            "what": "pinned host n,T,u -> rlb_init -> K steps -> rlb_macroscopic to pinned host"}
 
     batch = batch_sweep(torch, rlb, W, hbm_peak, local) if not args.no_batch else None
+    sphere = sphere_run(torch, rlb, W, local) if not args.no_batch else None
     if rank != 0:
         return 0
     l1 = l1_fp32_vs_fp64(torch)
@@ -418,6 +451,7 @@ def run_ours(args):
         "clocks": clk,
         "cpu_baseline": base,
         "batch": batch,
+        "sphere_cloud": sphere,
     }
     print(json.dumps(line), flush=True)
     if _dist is not None:
@@ -431,7 +465,8 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--no-batch", action="store_true", help="skip the 512-tube batched sweep")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 512-tube batched sweep and the sphere-cloud run")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
