@@ -93,10 +93,18 @@ typedef struct {
     int euler_mode;          /* 1: f <- f^eq, h <- h^eq of the streamed state (Sec. III) */
     int precision;           /* RLB_FP64 or RLB_FP32_STORAGE */
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
+    int symmetry_1d;         /* 1 (batched tubes only): exact 1-D symmetry reduction.  With
+                              * u_y = u_z = 0 and fields uniform in y and z, populations with
+                              * the same weight and the same c_x stay equal, leaving 7 classes
+                              * per distribution (rest, +x, -x, the y/z axis populations, the
+                              * diagonals with c_x = +2, with c_x = -2, the y-z diagonals); the
+                              * step updates one plane per class (14 population planes and 3
+                              * previous-level planes instead of 38 and 5).  Results equal the
+                              * 19-population step up to the rounding order of the moment sums. */
 } rlb_options;
 
 /* Fill *opts with the defaults: dt/dx 0.25, no overrides, viscous mode, FP64,
- * default stream. */
+ * default stream, no symmetry reduction. */
 RLB_API void rlb_default_options(rlb_options *opts);
 
 /* Validate a configuration on the host without touching the GPU.  Same
@@ -260,7 +268,8 @@ typedef struct {
  * through Eq. 56 per tube, as in rlb_create; opts->alpha_override >= 0 sets
  * one alpha for all tubes).  opts may be NULL: defaults of
  * rlb_default_options with precision RLB_FP32_STORAGE.  Requirements:
- * precision RLB_FP32_STORAGE, euler_mode 0, at most 2^30 stored cells
+ * precision RLB_FP32_STORAGE, euler_mode 0, symmetry_1d 0 or 1 (the tubes are
+ * 1-D with u_y = u_z = 0, so the reduction is exact), at most 2^30 stored cells
  * (each tube stored from a 128-byte boundary).  RLB_E_UNSTABLE if
  * 2 (c_0/c_t) dt/dx > 1 or 2 (c_0 nu / c_t) dt alpha_b > 1 for a tube.
  * Allocates 81 population and previous-level planes over the stored cells

@@ -119,6 +119,8 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.precision != RLB_FP64 && o.precision != RLB_FP32_STORAGE)
         return fail(ctx, RLB_E_INVALID, "unknown precision");
     if (o.euler_mode != 0 && o.euler_mode != 1) return fail(ctx, RLB_E_INVALID, "euler_mode must be 0 or 1");
+    if (o.symmetry_1d != 0)
+        return fail(ctx, RLB_E_INVALID, "the 1-D symmetry reduction is available for batched tubes (rlb_batch_create)");
     if (!std::isfinite(o.tau_override) || !std::isfinite(o.alpha_override))
         return fail(ctx, RLB_E_INVALID, "overrides must be finite");
     // explicit stability bounds
@@ -186,6 +188,7 @@ void rlb_default_options(rlb_options *o)
     o->euler_mode = 0;
     o->precision = RLB_FP64;
     o->cuda_stream = nullptr;
+    o->symmetry_1d = 0;
 }
 
 rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,

@@ -72,7 +72,7 @@ __device__ __forceinline__ f32::Geo tube_geo(int off, int nx, int x0)
 // update_pair).
 // MAXT = launch bound: 512 caps the kernel at 128 registers (some spill),
 // 384 at 168, 256 leaves it unconstrained; the autotuner picks.
-template <int LD, int MAXT>
+template <int LD, int MAXT, int NP>
 __global__ void __launch_bounds__(MAXT, 1) tubes_kernel(const Args a)
 {
     __shared__ int s_off[kMaxJobTubes], s_nx[kMaxJobTubes], s_steps[kMaxJobTubes], s_par[kMaxJobTubes];
@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(MAXT, 1) tubes_kernel(const Args a)
                     const bool odd = ((s_par[i] + s) & 1) != 0;
                     const float *f = odd ? a.f1 : a.f0, *h = odd ? a.h1 : a.h0;
                     float *fo = odd ? a.f0 : a.f1, *ho = odd ? a.h0 : a.h1;
-                    f32::update_pair<1, false, true, LD, f32::kParkOn, f32::kStageOn>(
+                    f32::update_pair<1, false, true, LD, f32::kParkOn, f32::kStageOn, NP>(
                         a.p, g, s_eos[i], s_kb[i], f, h, fo, ho, a.prev, a.ps, s_dyn + threadIdx.x,
                         int(blockDim.x), s_dyn + (f32::kParkOn ? f32::kParkSlots * blockDim.x : 0) + threadIdx.x,
                         int(blockDim.x));
@@ -135,10 +135,10 @@ __global__ void __launch_bounds__(MAXT, 1) tubes_kernel(const Args a)
     }
 }
 
-template <int LD, int MAXT>
+template <int LD, int MAXT, int NP>
 cudaError_t launch_variant(const Args &a, int threads, int cluster, cudaStream_t s, int *nclusters_out)
 {
-    auto kern = tubes_kernel<LD, MAXT>;
+    auto kern = tubes_kernel<LD, MAXT, NP>;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nclusters_out ? unsigned(cluster) : unsigned(a.nclusters * cluster), 1, 1);
     cfg.blockDim = dim3(unsigned(threads), 1, 1);
@@ -174,9 +174,15 @@ template <int LD>
 cudaError_t launch_ld(const Args &a, int threads, int bound, int cluster, cudaStream_t s, int *nclusters_out)
 {
     if (threads < 32 || threads > bound || threads % 32 != 0) return cudaErrorInvalidValue;
-    if (bound == 256) return launch_variant<LD, 256>(a, threads, cluster, s, nclusters_out);
-    if (bound == 384) return launch_variant<LD, 384>(a, threads, cluster, s, nclusters_out);
-    if (bound == 512) return launch_variant<LD, 512>(a, threads, cluster, s, nclusters_out);
+    if (a.np == 7) {
+        if (bound == 256) return launch_variant<LD, 256, 7>(a, threads, cluster, s, nclusters_out);
+        if (bound == 384) return launch_variant<LD, 384, 7>(a, threads, cluster, s, nclusters_out);
+        if (bound == 512) return launch_variant<LD, 512, 7>(a, threads, cluster, s, nclusters_out);
+        return cudaErrorInvalidValue;
+    }
+    if (bound == 256) return launch_variant<LD, 256, 19>(a, threads, cluster, s, nclusters_out);
+    if (bound == 384) return launch_variant<LD, 384, 19>(a, threads, cluster, s, nclusters_out);
+    if (bound == 512) return launch_variant<LD, 512, 19>(a, threads, cluster, s, nclusters_out);
     return cudaErrorInvalidValue;
 }
 

@@ -216,6 +216,7 @@ rlb::batch::Args make_args(rlb_batch *b)
     a.cl_start = b->d_cl;
     a.nclusters = b->nclusters;
     a.cluster = b->tune.cluster;
+    a.np = b->opt.symmetry_1d ? 7 : 19;
     a.f0 = b->f0;
     a.h0 = b->h0;
     a.f1 = b->f1;
@@ -325,6 +326,17 @@ rlb_status check_steps(rlb_batch *b, const long long *nsteps)
     return RLB_OK;
 }
 
+// under the 1-D symmetry reduction only the class representatives' planes
+// are current: copy them to the other populations of their classes
+rlb_status expand(rlb_batch *b)
+{
+    if (!b->opt.symmetry_1d) return RLB_OK;
+    RLB_BCUDA(b, rlb::batch::launch_tubes_expand(b->B, b->max_nx, b->d_tubes, b->d_par, b->ps, b->f0, b->h0, b->f1,
+                                                 b->h1, b->stream));
+    b->launches += 1;
+    return RLB_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -364,6 +376,7 @@ rlb_status rlb_batch_create(int B, const int *nx, const double *eta_over_s, cons
     if (o.precision != RLB_FP32_STORAGE)
         return bfail(nullptr, RLB_E_INVALID, "the batched path stores populations in FP32 (RLB_FP32_STORAGE)");
     if (o.euler_mode != 0) return bfail(nullptr, RLB_E_INVALID, "the batched path runs the viscous step only");
+    if (o.symmetry_1d != 0 && o.symmetry_1d != 1) return bfail(nullptr, RLB_E_INVALID, "symmetry_1d must be 0 or 1");
     if (limiter != RLB_LIMITER_MINMOD && limiter != RLB_LIMITER_NONE)
         return bfail(nullptr, RLB_E_INVALID, "unknown limiter");
     if (!(o.dt_over_dx > 0.0) || !std::isfinite(o.dt_over_dx))
@@ -558,6 +571,7 @@ rlb_status rlb_batch_macroscopic(rlb_batch *b, double *out, int on_device)
     if (!b) return bfail(nullptr, RLB_E_INVALID, "batch is NULL");
     if (!out) return bfail(b, RLB_E_INVALID, "out is NULL");
     RLB_BCUDA(b, cudaSetDevice(b->device));
+    if (rlb_status st = expand(b); st != RLB_OK) return st;
     double *dst = on_device ? out : b->stage;
     RLB_BCUDA(b, rlb::batch::launch_tubes_macro(b->B, b->max_nx, b->d_tubes, b->d_pack, b->d_par, b->ps, b->total,
                                                 b->f0, b->h0, b->f1, b->h1, dst, b->d_status, b->stream));
@@ -573,6 +587,7 @@ rlb_status rlb_batch_totals(rlb_batch *b, double *out)
     if (!b) return bfail(nullptr, RLB_E_INVALID, "batch is NULL");
     if (!out) return bfail(b, RLB_E_INVALID, "out is NULL");
     RLB_BCUDA(b, cudaSetDevice(b->device));
+    if (rlb_status st = expand(b); st != RLB_OK) return st;
     RLB_BCUDA(b, rlb::batch::launch_tubes_totals(b->B, b->d_tubes, b->d_par, b->ps, b->f0, b->h0, b->f1, b->h1,
                                                  b->d_tot, b->stream));
     b->launches += 1;

@@ -42,6 +42,37 @@ __global__ void tubes_macro_kernel(const Tube *__restrict__ tubes, const long lo
     macro_cell<float>((long long)t.off + x, ps, one ? f1 : f0, one ? h1 : h0, out, pack[b] + x, total, status);
 }
 
+// class of population i under the 1-D symmetry reduction, as the plane of
+// its representative: rest, +x, -x, y/z axis, x+ diagonals, x- diagonals,
+// y-z diagonals
+__device__ __forceinline__ int class_plane(int i)
+{
+    if (i < 3) return i;
+    if (i < 7) return 3;
+    if (i >= 15) return 15;
+    const int j = (i - 7) & 3;   // 7..10 and 11..14: signs (+,+) (+,-) (-,+) (-,-)
+    return j < 2 ? 7 : 9;
+}
+
+__global__ void tubes_expand_kernel(const Tube *__restrict__ tubes, const int *__restrict__ par, long long ps,
+                                    float *__restrict__ f0, float *__restrict__ h0, float *__restrict__ f1,
+                                    float *__restrict__ h1)
+{
+    const int b = blockIdx.y;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const Tube t = tubes[b];
+    if (x >= t.nx) return;
+    const bool one = par[b] != 0;
+    float *f = one ? f1 : f0, *h = one ? h1 : h0;
+    const long long idx = (long long)t.off + x;
+    for (int i = 3; i < 19; ++i) {
+        const int r = class_plane(i);
+        if (r == i) continue;
+        f[i * ps + idx] = f[r * ps + idx];
+        h[i * ps + idx] = h[r * ps + idx];
+    }
+}
+
 // one block per tube, fixed reduction order (deterministic)
 constexpr int kTubeTotBlock = 256;
 __global__ void __launch_bounds__(kTubeTotBlock) tubes_totals_kernel(const Tube *__restrict__ tubes,
@@ -102,6 +133,14 @@ cudaError_t launch_tubes_macro(int B, int max_nx, const Tube *tubes, const long 
 {
     const dim3 grid((max_nx + 127) / 128, B, 1);
     tubes_macro_kernel<<<grid, 128, 0, s>>>(tubes, pack, par, ps, total, f0, h0, f1, h1, out, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tubes_expand(int B, int max_nx, const Tube *tubes, const int *par, long long ps, float *f0,
+                                float *h0, float *f1, float *h1, cudaStream_t s)
+{
+    const dim3 grid((max_nx + 127) / 128, B, 1);
+    tubes_expand_kernel<<<grid, 128, 0, s>>>(tubes, par, ps, f0, h0, f1, h1);
     return cudaGetLastError();
 }
 

@@ -81,6 +81,7 @@ struct Args {
     const int *cl_start;    // [nclusters + 1]
     int nclusters;
     int cluster;            // blocks per cluster
+    int np;                 // planes updated per distribution: 19, or 7 under the 1-D symmetry reduction
     float *f0, *h0, *f1, *h1, *prev;
     long long ps;
 };
@@ -103,6 +104,11 @@ cudaError_t launch_tubes_macro(int B, int max_nx, const Tube *tubes, const long 
                                long long ps, long long total, const float *f0, const float *h0,
                                const float *f1, const float *h1, double *out, unsigned *status,
                                cudaStream_t s);
+// 1-D symmetry reduction: copy every class representative's plane into the
+// planes of the other populations of its class, in each tube's current
+// buffer, so that the full 19-population state is consistent again
+cudaError_t launch_tubes_expand(int B, int max_nx, const Tube *tubes, const int *par, long long ps, float *f0,
+                                float *h0, float *f1, float *h1, cudaStream_t s);
 // per-tube totals of T^00, T^0x, T^0y, T^0z, N^0: out[5 b + k]
 cudaError_t launch_tubes_totals(int B, const Tube *tubes, const int *par, long long ps, const float *f0,
                                 const float *h0, const float *f1, const float *h1, double *out,

@@ -40,6 +40,27 @@ __device__ __forceinline__ void for_pops(std::integer_sequence<int, Is...>, F &&
 }
 #define RLB_F32_POPS std::make_integer_sequence<int, 19>{}
 
+// Planes per distribution: NP = 19, or NP = 7 under the exact 1-D symmetry
+// (u_y = u_z = 0, fields uniform in y and z): then populations with the same
+// weight and the same c_x stay equal, and 7 classes remain per distribution:
+// rest, +x, -x, the four y/z axis populations, the four diagonals with
+// c_x = +2, the four with c_x = -2 and the four y-z diagonals.  Class k is
+// stored in the plane of its first population rep(k) and counts mult(k)
+// populations.
+template <int NP>
+__host__ __device__ constexpr int rep(int k)
+{
+    if constexpr (NP == 19) return k;
+    constexpr int r[7] = {0, 1, 2, 3, 7, 9, 15};
+    return r[k];
+}
+template <int NP>
+__host__ __device__ constexpr int mult(int k)
+{
+    if constexpr (NP == 19) return 1;
+    return k < 3 ? 1 : 4;
+}
+
 // geometry of one thread's pair of cells
 struct Geo {
     int idx0, idx1;      // cell indices (idx1 = idx0 when x0 + 1 is outside the grid)
@@ -441,16 +462,16 @@ constexpr int stage_slots()
 constexpr int kStageBufs = RLB_STAGE_BUFS;   // populations in flight: the one computed and the next ones
 constexpr int kStageAhead = kStageBufs - 1;  // prefetch distance in populations
 
-// Issue the copies of item J (J < 19: f population J, else h population
-// J - 19) into staging buffer J % kStageBufs: the same pairs, in the same
+// Issue the copies of item J (J < NP: f class J, else h class J - NP) into
+// staging buffer J % kStageBufs: the same pairs, in the same
 // slots, that streamed2 reads through StageSrc.  dst0 = shared address of
 // slot 0 of buffer 0 of this thread, sstride = bytes between slots.
-template <int DIM, int J>
+template <int DIM, int NP, int J>
 __device__ __forceinline__ void stage_item(const float *f, const float *h, const Geo &g, const StepParams &p,
                                            long long ps, unsigned dst0, unsigned sstride)
 {
-    constexpr bool IS_F = J < 19;
-    constexpr int I = IS_F ? J : J - 19;
+    constexpr bool IS_F = J < NP;
+    constexpr int I = rep<NP>(IS_F ? J : J - NP);
     constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
     constexpr bool need_lap = IS_F && I != 0;
     const float *q = (IS_F ? f : h) + I * ps + g.idx0;
@@ -495,7 +516,11 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
 // kStageAhead populations ahead of its use (stage_item), so that the loads of the next
 // populations are in flight while one is computed; stage = slot 0 of buffer
 // 0 of this thread, sstride = f2 elements between slots.
-template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false>
+//
+// NP = 7: the 1-D symmetry reduction (see rep and mult); only the planes of
+// the 7 class representatives are read and written, and the previous level's
+// planes of sum c_y f and sum c_z f (zero) are left alone.
+template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false, int NP = 19>
 __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
                                             const float *__restrict__ f, const float *__restrict__ h,
                                             float *__restrict__ fo, float *__restrict__ ho,
@@ -505,26 +530,28 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
 {
     const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim;
     static_assert(!STAGE || (VEC2 && !EULER), "staging needs aligned pairs and the viscous step");
+    static_assert(NP == 19 || (NP == 7 && DIM == 1 && !EULER), "the symmetry reduction is 1-D, viscous");
+    constexpr int NI = 2 * NP;   // items: f classes, then h classes
     unsigned sdst0 = 0;
     if constexpr (STAGE) {
         sdst0 = unsigned(__cvta_generic_to_shared(stage));
         for_pops(std::make_integer_sequence<int, kStageAhead>{}, [&](auto jc) {
-            stage_item<DIM, decltype(jc)::value>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
+            stage_item<DIM, NP, decltype(jc)::value>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
         });
     }
-    // the explicit part of item J (J < 19: f population J, else h population J - 19)
+    // the explicit part of item J (J < NP: f class J, else h class J - NP)
     auto item = [&](auto jc) -> f2 {
         constexpr int J = decltype(jc)::value;
-        constexpr bool IS_F = J < 19;
-        constexpr int I = IS_F ? J : J - 19;
+        constexpr bool IS_F = J < NP;
+        constexpr int I = rep<NP>(IS_F ? J : J - NP);
         const float *q = (IS_F ? f : h) + I * ps;
         const float ghost = IS_F ? p.f_ghost_f[I] : p.f_ghost_h[I];
         if constexpr (STAGE) {
-            if constexpr (J + kStageAhead < 38) {
-                stage_item<DIM, J + kStageAhead>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
+            if constexpr (J + kStageAhead < NI) {
+                stage_item<DIM, NP, J + kStageAhead>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
                 cp_wait<kStageAhead>();
             } else {
-                cp_wait<37 - J>();   // the groups issued after item J's
+                cp_wait<NI - 1 - J>();   // the groups issued after item J's
             }
             const StageSrc src{stage + (J % kStageBufs) * stage_slots<DIM>() * sstride, sstride};
             return streamed2<DIM, IS_F, I, VEC2, LD>(src, q, g, p, ghost, k1, k2, hl, kb);
@@ -538,15 +565,24 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         // raw sums of the local populations: S = sum f, V_a = sum c_a f
         // (double-float), Sh = sum h
         df2 S{bc(0.0f), bc(0.0f)}, Vx = S, Vy = S, Vz = S, Hs = S;
-        for_pops(RLB_F32_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
+        for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int I = rep<NP>(k), m = mult<NP>(k);
             const f2 v = ldpair<VEC2, LD>(f + I * ps, g, 0);
-            acc(S, v);
+            // m c_i v with m and c_i powers of two: exact
+            auto scaled = [&](auto wc) {
+                constexpr int w = decltype(wc)::value;
+                return w == 1 ? v : (w == -1 ? -v : bc(float(w)) * v);
+            };
+            acc(S, scaled(std::integral_constant<int, m>{}));
             constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
-            if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
-            if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
-            if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
-            acc(Hs, ldpair<VEC2, LD>(h + I * ps, g, 0));
+            if constexpr (cx != 0) acc(Vx, scaled(std::integral_constant<int, cx * m>{}));
+            if constexpr (NP == 19) {   // under the reduction sum c_y f = sum c_z f = 0
+                if constexpr (cy != 0) acc(Vy, scaled(std::integral_constant<int, cy>{}));
+                if constexpr (cz != 0) acc(Vz, scaled(std::integral_constant<int, cz>{}));
+            }
+            const f2 hv = ldpair<VEC2, LD>(h + I * ps, g, 0);
+            acc(Hs, m == 1 ? hv : bc(float(m)) * hv);
         });
         const f2 Sh = Hs.hi + Hs.lo;
         bool ok0, ok1;
@@ -571,8 +607,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         // targets of 2 f^eq(t) - f^eq(t - dt) are exact: T = 2 S(t) - S(t - dt)
         const f2 Sp = ldpair<VEC2, LD>(prev + 0 * ps, g, 0);
         const f2 Vpx = ldpair<VEC2, LD>(prev + 1 * ps, g, 0);
-        const f2 Vpy = ldpair<VEC2, LD>(prev + 2 * ps, g, 0);
-        const f2 Vpz = ldpair<VEC2, LD>(prev + 3 * ps, g, 0);
+        const f2 Vpy = NP == 19 ? ldpair<VEC2, LD>(prev + 2 * ps, g, 0) : bc(0.0f);
+        const f2 Vpz = NP == 19 ? ldpair<VEC2, LD>(prev + 3 * ps, g, 0) : bc(0.0f);
         const f2 Shp = ldpair<VEC2, LD>(prev + 4 * ps, g, 0);
         const Mac2 mp = recover2f(Sp, Vpx, Vpy, Vpz, Shp);
         const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
@@ -612,8 +648,10 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
             // the raw sums of this level become the next step's previous level
             stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
             stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
-            stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
-            stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
+            if constexpr (NP == 19) {
+                stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
+                stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
+            }
             stpair<VEC2>(prev + 4 * ps, g, Sh);
             if constexpr (PARK) {
                 park[0] = H0;
@@ -625,9 +663,10 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                     park[(7 + j) * pstride] = Ho[j];
                 }
             }
-            for_pops(RLB_F32_POPS, [&](auto ic) {
-                constexpr int I = decltype(ic)::value;
-                const f2 pre = item(std::integral_constant<int, I>{});
+            for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int I = rep<NP>(k);
+                const f2 pre = item(std::integral_constant<int, k>{});
                 stpair<VEC2>(fo + I * ps, g, fma2(kap, eq2<I>(ef) - pre, pre));
             });
         }
@@ -643,9 +682,10 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                 }
             }
             const W2 eh = weigh2(H0, Hb, Hd, Ho, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
-            for_pops(RLB_F32_POPS, [&](auto ic) {
-                constexpr int I = decltype(ic)::value;
-                const f2 pre = item(std::integral_constant<int, 19 + I>{});
+            for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
+                constexpr int k = decltype(kc)::value;
+                constexpr int I = rep<NP>(k);
+                const f2 pre = item(std::integral_constant<int, NP + k>{});
                 stpair<VEC2>(ho + I * ps, g, fma2(kap, eq2<I>(eh) - pre, pre));
             });
         }

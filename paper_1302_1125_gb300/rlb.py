@@ -34,7 +34,7 @@ class rlb_grid(C.Structure):
 class rlb_options(C.Structure):
     _fields_ = [("dt_over_dx", C.c_double), ("tau_override", C.c_double),
                 ("alpha_override", C.c_double), ("euler_mode", C.c_int),
-                ("precision", C.c_int), ("cuda_stream", C.c_void_p)]
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("symmetry_1d", C.c_int)]
 
 
 class rlb_batch_tuning(C.Structure):
@@ -154,9 +154,9 @@ def make_grid(nx, ny=1, nz=1, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
 
 
 def make_options(dt_over_dx=0.25, tau_override=0.0, alpha_override=-1.0, euler_mode=0,
-                 precision=FP64, cuda_stream=None):
+                 precision=FP64, cuda_stream=None, symmetry_1d=0):
     return rlb_options(float(dt_over_dx), float(tau_override), float(alpha_override),
-                       int(euler_mode), int(precision), cuda_stream)
+                       int(euler_mode), int(precision), cuda_stream, int(symmetry_1d))
 
 
 def rlb_check_config(grid, Q, eta_over_s, zeta_over_s, limiter, opts) -> int:
@@ -398,13 +398,13 @@ class Batch:
     """B independent 1-D tubes advanced by one persistent launch (FP32 storage)."""
 
     def __init__(self, nx, eta_over_s, zeta_over_s, *, limiter=LIMITER_MINMOD, dt_over_dx=0.15,
-                 tau_override=0.0, alpha_override=-1.0, stream="current"):
+                 tau_override=0.0, alpha_override=-1.0, symmetry_1d=0, stream="current"):
         self.nx = _i32(nx)
         self.B = int(self.nx.size)
         self.eta = np.ascontiguousarray(eta_over_s, np.float64)
         self.zeta = np.ascontiguousarray(zeta_over_s, np.float64)
         s = _current_stream() if stream == "current" else stream
-        self._opts = make_options(dt_over_dx, tau_override, alpha_override, 0, FP32_STORAGE, s)
+        self._opts = make_options(dt_over_dx, tau_override, alpha_override, 0, FP32_STORAGE, s, symmetry_1d)
         h = C.c_void_p()
         dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
         _bcheck(lib().rlb_batch_create(self.B, self.nx.ctypes.data_as(ip), self.eta.ctypes.data_as(dp),

@@ -54,7 +54,7 @@ def cfg(**kw):
     for k in list(kw):
         if k in g:
             g[k] = kw.pop(k)
-        elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision"):
+        elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision", "symmetry_1d"):
             o[k] = kw.pop(k)
     return rlb.make_grid(**g), rlb.make_options(**o), kw
 
@@ -77,6 +77,7 @@ def cfg(**kw):
     ({"alpha_override": 1.0}, rlb.RLB_E_UNSTABLE),       # 2 (c0 nu/ct) dt alpha > 1
     ({"alpha_override": 0.5}, rlb.RLB_OK),
     ({"dt_over_dx": -1.0}, rlb.RLB_E_INVALID),
+    ({"symmetry_1d": 1}, rlb.RLB_E_INVALID),     # batched tubes only
 ])
 def test_host_validation(lib, change, expect):
     change = dict(change)

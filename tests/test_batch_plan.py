@@ -141,6 +141,7 @@ def test_plan_rejects_bad_inputs():
     (dict(dt_over_dx=0.73), rlb.RLB_E_UNSTABLE),
     (dict(alpha_override=1.0), rlb.RLB_E_UNSTABLE),
     (dict(zeta=[0.0, 1e6]), rlb.RLB_E_UNSTABLE),
+    (dict(symmetry_1d=2), rlb.RLB_E_INVALID),
 ])
 def test_batch_create_validates_on_the_host(kw, expect):
     import ctypes as C
@@ -148,7 +149,8 @@ def test_batch_create_validates_on_the_host(kw, expect):
     eta = np.asarray(kw.get("eta", [0.1] * max(nx.size, 1)), np.float64)
     zeta = np.asarray(kw.get("zeta", [0.0] * max(nx.size, 1)), np.float64)
     o = rlb.make_options(dt_over_dx=kw.get("dt_over_dx", 0.25), alpha_override=kw.get("alpha_override", -1.0),
-                         euler_mode=kw.get("euler_mode", 0), precision=kw.get("precision", rlb.FP32_STORAGE))
+                         euler_mode=kw.get("euler_mode", 0), precision=kw.get("precision", rlb.FP32_STORAGE),
+                         symmetry_1d=kw.get("symmetry_1d", 0))
     h = C.c_void_p()
     dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
     st = rlb.lib().rlb_batch_create(int(nx.size), nx.ctypes.data_as(ip), eta.ctypes.data_as(dp),
