@@ -51,7 +51,7 @@ class _Params(C.Structure):
                 ("zeta_over_s", C.c_double), ("tau_override", C.c_double),
                 ("alpha_override", C.c_double), ("inlet_n", C.c_double),
                 ("inlet_T", C.c_double), ("inlet_u", C.c_double * 3),
-                ("limiter", C.c_int), ("euler_mode", C.c_int)]
+                ("limiter", C.c_int), ("euler_mode", C.c_int), ("model", C.c_int)]
 
 
 _lib = None
@@ -91,6 +91,8 @@ def lib():
         _lib.orc_macroscopic.argtypes = [C.POINTER(_Params), dp, dp, dp]
         _lib.orc_macroscopic.restype = C.c_long
         _lib.orc_nu.restype = C.c_double
+        _lib.orc_set_model.argtypes = [C.c_int]
+        _lib.orc_get_model.restype = C.c_int
         _lib.orc_set_threads.argtypes = [C.c_int]
         _lib.orc_get_threads.restype = C.c_int
     return _lib
@@ -101,8 +103,14 @@ def _p(a: np.ndarray):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def nu() -> float:
-    """the global lattice constant nu = c/c_s of the oracle (sqrt(13))"""
+def set_model(model: int) -> None:
+    """lattice used by the functions without Params: 0 extended, 1 basic"""
+    lib().orc_set_model(int(model))
+
+
+def nu(model: int = 0) -> float:
+    """the lattice constant nu = c/c_s: sqrt(13) (extended), sqrt(19) (basic)"""
+    set_model(model)
     return float(lib().orc_nu())
 
 
@@ -131,6 +139,7 @@ class Params:
     inlet_u: tuple = (0.0, 0.0, 0.0)
     limiter: int = LIMITER_MINMOD
     euler_mode: int = 0
+    model: int = 0          # 0 extended lattice (Sec. II.A), 1 basic lattice (Sec. II)
 
     @property
     def N(self) -> int:
@@ -140,11 +149,12 @@ class Params:
         g = _Grid(self.nx, self.ny, self.nz, (C.c_int * 3)(*self.bc_lo), (C.c_int * 3)(*self.bc_hi))
         return _Params(g, self.dt, self.eta_over_s, self.zeta_over_s, self.tau_override,
                        self.alpha_override, self.inlet_n, self.inlet_T,
-                       (C.c_double * 3)(*self.inlet_u), self.limiter, self.euler_mode)
+                       (C.c_double * 3)(*self.inlet_u), self.limiter, self.euler_mode, self.model)
 
 
-def lattice():
+def lattice(model: int = 0):
     """(e[19,3] int, c[19,3], w[19], wh[19], xi0) as the oracle builds them."""
+    set_model(model)
     e = np.zeros((19, 3), np.int32)
     c = np.zeros((19, 3))
     w = np.zeros(19)
@@ -153,26 +163,30 @@ def lattice():
     return e, c, w, wh, xi0
 
 
-def feq(P: float, up) -> np.ndarray:
+def feq(P: float, up, model: int = 0) -> np.ndarray:
+    set_model(model)
     out = np.zeros(19)
     lib().orc_feq(float(P), _p(np.ascontiguousarray(up, np.float64)), _p(out))
     return out
 
 
-def heq(n: float, up) -> np.ndarray:
+def heq(n: float, up, model: int = 0) -> np.ndarray:
+    set_model(model)
     out = np.zeros(19)
     lib().orc_heq(float(n), _p(np.ascontiguousarray(up, np.float64)), _p(out))
     return out
 
 
-def moments(f, h) -> np.ndarray:
+def moments(f, h, model: int = 0) -> np.ndarray:
+    set_model(model)
     out = np.zeros(5)
     lib().orc_moments(_p(np.ascontiguousarray(f, np.float64)),
                       _p(np.ascontiguousarray(h, np.float64)), _p(out))
     return out
 
 
-def recover(mom):
+def recover(mom, model: int = 0):
+    set_model(model)
     out = np.zeros(5)
     bad = lib().orc_recover(_p(np.ascontiguousarray(mom, np.float64)), _p(out))
     return out, bool(bad)

@@ -53,6 +53,21 @@
  *      (Sec. III, astrophysical application).
  *  R10 Euler (inviscid) mode replaces the collision by f <- f^eq, h <- h^eq of
  *      the streamed state (Sec. III).
+ *  R11 solid cells (orc_solid_reset): every cell of the cloud is set to the
+ *      equilibrium of its fixed state after every step.
+ *  R13 the basic model (Sec. II, before the extension; model = 1) is the
+ *      D3Q19 lattice with unit diagonals c_a (+-1, +-1, 0), weights of its
+ *      own quadrature, c_a = sqrt(19)/nu and c_t/c_0 = sqrt(27)/nu; as R1,
+ *      nu = sqrt(19) so that c_a = 1 and the weights are -44/361, 99/722,
+ *      9/361.  Everything else is the same step (Eq. 57: limiter streaming,
+ *      bulk term, implicit collision), so the two models differ only in the
+ *      lattice.  The equilibrium is again the second-order polynomial matched
+ *      to Eq. 36 (R8); the paper's constants make it exist on both lattices.
+ *  R14 the paper gives number-distribution weights (Eqs. 59-60) only for
+ *      the extended cell configuration; on the basic lattice the weights
+ *      that give Eq. 58 the same moments (sum_i w'_i = 1 and
+ *      sum_i w'_i c_ix^2 = 1/3, so that N^0 = n gamma) and fourth-order
+ *      isotropy are the standard D3Q19 weights 1/3, 1/18, 1/36.
  */
 #include "rlb_oracle.h"
 
@@ -63,16 +78,18 @@
 #include <omp.h>
 #endif
 
-#define NU 3.6055512754639891   /* sqrt(13), R1 */
+#define NU (L->nu)          /* the model's lattice constant nu: sqrt(13) (R1) or sqrt(19) (R13) */
 #define D_G 16.0          /* gluon degeneracy, Sec. III */
 #define S_MIN 1e-3        /* R7 */
 #define T_REF 1.0         /* R1 / R4 */
 #define PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------ */
-/* Lattice: the extended D3Q19 configuration of Sec. II.A.                   */
+/* Lattices: the extended D3Q19 configuration of Sec. II.A (model 0) and the */
+/* basic D3Q19 lattice of Sec. II (model 1, R13).                            */
 /* ------------------------------------------------------------------------ */
 typedef struct {
+    double nu;             /* lattice constant nu = c/c_s (R1, R13) */
     int e[19][3];          /* unit direction of each population */
     double c[19][3];       /* spatial components c_i of xi_i (Eq. 42) */
     double w[19];          /* Eqs. 43-45 */
@@ -84,70 +101,98 @@ typedef struct {
     double m22;            /* sum_i w_i c_ix^2 c_iy^2 */
 } lattice_t;
 
-static lattice_t L;
+static lattice_t L_models[2];
+static const lattice_t *L = &L_models[0];
 
-__attribute__((constructor)) static void build_lattice(void)
+static void build_lattice(lattice_t *l, int basic)
 {
-    const double ca = sqrt(13.0) / NU;            /* Eq. 46 */
-    const double ct_c0 = sqrt(27.0) / NU;         /* Eq. 46 */
+    const double nu = basic ? sqrt(19.0) : sqrt(13.0);   /* R1, R13 */
+    const double ca = (basic ? sqrt(19.0) : sqrt(13.0)) / nu;   /* Eq. 46 / Sec. II */
+    const double ct_c0 = sqrt(27.0) / nu;                 /* Eq. 46 / Sec. II */
+    const double dshell = basic ? 1.0 : 2.0;              /* diagonal length in units of c_a */
     int i = 0, a, b, s1, s2;
-    memset(&L, 0, sizeof(L));
+    memset(l, 0, sizeof(*l));
+    l->nu = nu;
     /* i = 0: rest */
     i = 1;
     /* 1 <= i <= 6: c_a (+-1, 0, 0) fully symmetric */
     for (a = 0; a < 3; ++a)
         for (s1 = 1; s1 >= -1; s1 -= 2) {
-            L.e[i][a] = s1;
-            L.c[i][a] = ca * s1;
+            l->e[i][a] = s1;
+            l->c[i][a] = ca * s1;
             ++i;
         }
-    /* 7 <= i <= 18: 2 c_a (+-1, +-1, 0) fully symmetric */
+    /* 7 <= i <= 18: 2 c_a (+-1, +-1, 0) (extended) or c_a (+-1, +-1, 0) (basic) */
     for (a = 0; a < 3; ++a)
         for (b = a + 1; b < 3; ++b)
             for (s1 = 1; s1 >= -1; s1 -= 2)
                 for (s2 = 1; s2 >= -1; s2 -= 2) {
-                    L.e[i][a] = s1;
-                    L.e[i][b] = s2;
-                    L.c[i][a] = 2.0 * ca * s1;
-                    L.c[i][b] = 2.0 * ca * s2;
+                    l->e[i][a] = s1;
+                    l->e[i][b] = s2;
+                    l->c[i][a] = dshell * ca * s1;
+                    l->c[i][b] = dshell * ca * s2;
                     ++i;
                 }
-    /* weights, Eqs. 43-45, written as printed with c_t/c_0, c_a, nu */
+    /* weights written as printed with c_t/c_0, c_a, nu: Eqs. 43-45 (extended)
+     * and the basic model's quadrature weights of Sec. II */
     {
         const double r2 = ct_c0 * ct_c0;  /* c_t^2 / c_0^2 */
-        const double w0 = 1.0 + 7.0 * r2 * NU * NU / 676.0 - r2 / (ca * ca);
-        const double w1 = r2 / (1014.0 * ca * ca) * (169.0 - 2.0 * ca * ca * NU * NU);
-        const double w2 = r2 * NU * NU / 8112.0;
-        L.w[0] = w0;
-        for (i = 1; i <= 6; ++i) L.w[i] = w1;
-        for (i = 7; i <= 18; ++i) L.w[i] = w2;
+        double w0, w1, w2;
+        if (basic) {
+            w0 = 1.0 + 4.0 * r2 * nu * nu / 361.0 - r2 / (ca * ca);
+            w1 = r2 / (2166.0 * ca * ca) * (361.0 - 8.0 * ca * ca * nu * nu);
+            w2 = r2 * nu * nu / 1083.0;
+        } else {
+            w0 = 1.0 + 7.0 * r2 * nu * nu / 676.0 - r2 / (ca * ca);
+            w1 = r2 / (1014.0 * ca * ca) * (169.0 - 2.0 * ca * ca * nu * nu);
+            w2 = r2 * nu * nu / 8112.0;
+        }
+        l->w[0] = w0;
+        for (i = 1; i <= 6; ++i) l->w[i] = w1;
+        for (i = 7; i <= 18; ++i) l->w[i] = w2;
     }
-    /* number-distribution weights, Eqs. 59-60 (c_a is the scalar of Eq. 46) */
-    L.wh[0] = 1.0 / 10.0;
-    for (i = 1; i <= 6; ++i) L.wh[i] = 6.0 / 35.0 - 1.0 / (42.0 * ca * ca);
-    for (i = 7; i <= 18; ++i) L.wh[i] = 1.0 / (84.0 * ca * ca) - 3.0 / 280.0;
-    L.xi0 = ct_c0;
-    L.c0_over_ct = 1.0 / ct_c0;
+    /* number-distribution weights: Eqs. 59-60 (extended; c_a is the scalar of
+     * Eq. 46), the standard D3Q19 weights on the basic lattice (R14) */
+    if (basic) {
+        l->wh[0] = 1.0 / 3.0;
+        for (i = 1; i <= 6; ++i) l->wh[i] = 1.0 / 18.0;
+        for (i = 7; i <= 18; ++i) l->wh[i] = 1.0 / 36.0;
+    } else {
+        l->wh[0] = 1.0 / 10.0;
+        for (i = 1; i <= 6; ++i) l->wh[i] = 6.0 / 35.0 - 1.0 / (42.0 * ca * ca);
+        for (i = 7; i <= 18; ++i) l->wh[i] = 1.0 / (84.0 * ca * ca) - 3.0 / 280.0;
+    }
+    l->xi0 = ct_c0;
+    l->c0_over_ct = 1.0 / ct_c0;
     /* lattice moments used to solve the moment conditions of Eq. 36 (R8) */
     for (i = 0; i < 19; ++i) {
-        L.sigma2 += L.w[i] * L.c[i][0] * L.c[i][0];
-        L.m4 += L.w[i] * pow(L.c[i][0], 4);
-        L.m22 += L.w[i] * L.c[i][0] * L.c[i][0] * L.c[i][1] * L.c[i][1];
+        l->sigma2 += l->w[i] * l->c[i][0] * l->c[i][0];
+        l->m4 += l->w[i] * pow(l->c[i][0], 4);
+        l->m22 += l->w[i] * l->c[i][0] * l->c[i][0] * l->c[i][1] * l->c[i][1];
     }
 }
+
+__attribute__((constructor)) static void build_lattices(void)
+{
+    build_lattice(&L_models[0], 0);
+    build_lattice(&L_models[1], 1);
+}
+
+void orc_set_model(int model) { L = &L_models[model == 1 ? 1 : 0]; }
+int orc_get_model(void) { return L == &L_models[1] ? 1 : 0; }
 
 double orc_lattice(int *e, double *c, double *w, double *wh)
 {
     int i, a;
     for (i = 0; i < 19; ++i) {
         for (a = 0; a < 3; ++a) {
-            if (e) e[3 * i + a] = L.e[i][a];
-            if (c) c[3 * i + a] = L.c[i][a];
+            if (e) e[3 * i + a] = L->e[i][a];
+            if (c) c[3 * i + a] = L->c[i][a];
         }
-        if (w) w[i] = L.w[i];
-        if (wh) wh[i] = L.wh[i];
+        if (w) w[i] = L->w[i];
+        if (wh) wh[i] = L->wh[i];
     }
-    return L.xi0;
+    return L->xi0;
 }
 
 double orc_nu(void) { return NU; }
@@ -174,20 +219,20 @@ void orc_feq(double P, const double up[3], double out[19])
 {
     const double u2 = up[0] * up[0] + up[1] * up[1] + up[2] * up[2];
     const double gamma = sqrt(1.0 + u2);      /* Eq. 8 with nu = 1 */
-    const double a0 = P / L.sigma2;
-    const double a1 = 4.0 * P * gamma / (L.xi0 * L.sigma2);
-    const double a2 = 4.0 * P / L.m22;
-    const double a3 = 4.0 * P / (L.m4 - L.m22);
-    const double a4 = -a3 * L.m22 / L.sigma2;
+    const double a0 = P / L->sigma2;
+    const double a1 = 4.0 * P * gamma / (L->xi0 * L->sigma2);
+    const double a2 = 4.0 * P / L->m22;
+    const double a3 = 4.0 * P / (L->m4 - L->m22);
+    const double a4 = -a3 * L->m22 / L->sigma2;
     int i;
     for (i = 0; i < 19; ++i) {
-        const double *c = L.c[i];
+        const double *c = L->c[i];
         const double cu = c[0] * up[0] + c[1] * up[1] + c[2] * up[2];
         const double off = c[0] * c[1] * up[0] * up[1] + c[0] * c[2] * up[0] * up[2]
                          + c[1] * c[2] * up[1] * up[2];
         const double dia = c[0] * c[0] * up[0] * up[0] + c[1] * c[1] * up[1] * up[1]
                          + c[2] * c[2] * up[2] * up[2];
-        out[i] = L.w[i] * (a0 + a1 * cu + a2 * off + a3 * dia + a4 * u2);
+        out[i] = L->w[i] * (a0 + a1 * cu + a2 * off + a3 * dia + a4 * u2);
     }
 }
 
@@ -200,8 +245,8 @@ void orc_heq(double n, const double up[3], double out[19])
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     int i;
     for (i = 0; i < 19; ++i) {
-        const double cu = L.c[i][0] * u[0] + L.c[i][1] * u[1] + L.c[i][2] * u[2];
-        out[i] = L.wh[i] * n * gamma * (L.c0_over_ct + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+        const double cu = L->c[i][0] * u[0] + L->c[i][1] * u[1] + L->c[i][2] * u[2];
+        out[i] = L->wh[i] * n * gamma * (L->c0_over_ct + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
     }
 }
 
@@ -215,9 +260,9 @@ void orc_moments(const double f[19], const double h[19], double mom[5])
     int i, a;
     for (a = 0; a < 5; ++a) mom[a] = 0.0;
     for (i = 0; i < 19; ++i) {
-        mom[0] += L.xi0 * L.xi0 * f[i];
-        for (a = 0; a < 3; ++a) mom[1 + a] += L.xi0 * L.c[i][a] * f[i];
-        mom[4] += L.xi0 * h[i];
+        mom[0] += L->xi0 * L->xi0 * f[i];
+        for (a = 0; a < 3; ++a) mom[1 + a] += L->xi0 * L->c[i][a] * f[i];
+        mom[4] += L->xi0 * h[i];
     }
 }
 
@@ -250,6 +295,7 @@ int orc_recover(const double mom[5], double macro[5])
  * and T = P/n (Sec. III: P = n T). */
 double orc_tau(const orc_params *p, double P, double n)
 {
+    orc_set_model(p->model);
     double T, neq, lam, sfac, s, eta;
     if (p->tau_override > 0.0) return p->tau_override;
     T = P / n;
@@ -265,6 +311,7 @@ double orc_tau(const orc_params *p, double P, double n)
 /* alpha of Eq. 55 from zeta/s through Eq. 56 (R4) */
 double orc_alpha(const orc_params *p)
 {
+    orc_set_model(p->model);
     double nref, sref, pref, eta_b;
     if (p->alpha_override >= 0.0) return p->alpha_override;
     nref = D_G * T_REF * T_REF * T_REF / (PI * PI);   /* lambda = 1 */
@@ -431,18 +478,18 @@ static int update_cell(const orc_params *p, const step_consts *k, const plane_re
     const long idx = x + (long)p->g.nx * (y + (long)p->g.ny * z);
     const double dt = p->dt;
     /* prefactor of the flux term of Eq. 57: (c0/ct)(dt/dx); p_i^a = c_ia */
-    const double kstream = L.c0_over_ct * dt;
+    const double kstream = L->c0_over_ct * dt;
     /* prefactor of the bulk term of Eq. 57 times lambda_i (Eq. 55, dx = 1) */
-    const double kbulk = L.c0_over_ct * NU * dt * k->alpha;
+    const double kbulk = L->c0_over_ct * NU * dt * k->alpha;
     double f[19], h[19], sf[19], sh[19], mom[5], mac[5];
     int i, bad;
 
     for (i = 0; i < 19; ++i) {
         f[i] = get(F, i, idx);
         h[i] = get(H, i, idx);
-        sf[i] = stream_at(p, F, i, k->ghost_f[i], L.c[i], kstream, x, y, z);
+        sf[i] = stream_at(p, F, i, k->ghost_f[i], L->c[i], kstream, x, y, z);
         if (i != 0) sf[i] += kbulk * lap_at(p, F, i, k->ghost_f[i], x, y, z);  /* lambda_0 = 0 */
-        sh[i] = stream_at(p, H, i, k->ghost_h[i], L.c[i], kstream, x, y, z);  /* no lambda term */
+        sh[i] = stream_at(p, H, i, k->ghost_h[i], L->c[i], kstream, x, y, z);  /* no lambda term */
     }
 
     if (p->euler_mode) {
@@ -466,7 +513,7 @@ static int update_cell(const orc_params *p, const step_consts *k, const plane_re
         orc_feq(pv[0], pv + 1, feqp);   /* f^eq(x, t - dt) */
         orc_heq(pv[4], pv + 1, heqp);
         tau = orc_tau(p, mac[0], mac[4]);
-        omega = L.c0_over_ct * NU * dt / tau;
+        omega = L->c0_over_ct * NU * dt / tau;
         /* Eq. 57 solved for f(x, t + dt) */
         for (i = 0; i < 19; ++i) {
             fo[i] = (f[i] + sf[i] + omega * (2.0 * feq[i] - feqp[i])) / (1.0 + omega);
@@ -481,6 +528,7 @@ void orc_init(const orc_params *p, const double *n, const double *T,
               const double *ux, const double *uy, const double *uz,
               double *f, double *h, double *prev)
 {
+    orc_set_model(p->model);
     const long N = (long)p->g.nx * p->g.ny * p->g.nz;
     long idx;
 #pragma omp parallel for schedule(static) num_threads(g_threads)
@@ -508,6 +556,7 @@ void orc_init(const orc_params *p, const double *n, const double *T,
 void orc_solid_reset(const orc_params *p, const unsigned char *mask, double n, double T,
                      double *f, double *h, double *prev)
 {
+    orc_set_model(p->model);
     const long N = (long)p->g.nx * p->g.ny * p->g.nz;
     const double rest[3] = {0.0, 0.0, 0.0};
     double fe[19], he[19];
@@ -532,6 +581,7 @@ void orc_solid_reset(const orc_params *p, const unsigned char *mask, double n, d
 long orc_step(const orc_params *p, const double *f, const double *h,
               double *prev, double *fout, double *hout)
 {
+    orc_set_model(p->model);
     const long N = (long)p->g.nx * p->g.ny * p->g.nz;
     const plane_ref F = {f, 0, N}, H = {h, 0, N}, PV = {prev, 0, N};
     step_consts k;
@@ -559,6 +609,7 @@ long orc_step_cells(const orc_params *p, const void *f, const void *h,
                     const void *prev, int is_f32, long ncell, const long *cells,
                     double *fout, double *hout, double *mout)
 {
+    orc_set_model(p->model);
     const long N = (long)p->g.nx * p->g.ny * p->g.nz;
     const plane_ref F = {f, is_f32, N}, H = {h, is_f32, N}, PV = {prev, is_f32, N};
     step_consts k;
@@ -575,6 +626,7 @@ long orc_step_cells(const orc_params *p, const void *f, const void *h,
 
 long orc_macroscopic(const orc_params *p, const double *f, const double *h, double *out)
 {
+    orc_set_model(p->model);
     const long N = (long)p->g.nx * p->g.ny * p->g.nz;
     long idx, bad = 0;
 #pragma omp parallel for schedule(static) reduction(+ : bad) num_threads(g_threads)

@@ -18,7 +18,8 @@
  *                 (u' = gamma*u, the spatial part of U^mu)
  *   macroscopic   6 planes: n, e, u_x, u_y, u_z, gamma (u = 3-velocity)
  *
- * Lattice units: nu = sqrt(13) so c_a = 1; c_i = c_a * shell * direction.
+ * Lattice units: nu = sqrt(13) so c_a = 1; c_i = c_a * shell * direction
+ * (basic lattice: nu = sqrt(19), c_a = 1, diagonals c_a (+-1, +-1, 0)).
  * Population order (extended lattice, Sec. II.A, Eq. 42):
  *   0        rest
  *   1..6     c_a * (+x, -x, +y, -y, +z, -z)
@@ -51,8 +52,13 @@ typedef struct {
     double inlet_n, inlet_T, inlet_u[3];  /* state of the inlet ghost cells */
     int limiter;                 /* ORC_LIMITER_* */
     int euler_mode;              /* 1: f <- f^eq of the streamed state (Sec. III) */
+    int model;                   /* 0: extended lattice (Sec. II.A), 1: basic lattice (Sec. II, R13) */
 } orc_params;
 
+/* the lattice the functions below without an orc_params use: 0 extended
+ * (default), 1 basic; the functions taking orc_params select p->model */
+void orc_set_model(int model);
+int orc_get_model(void);
 double orc_nu(void);
 /* lattice: e[19][3] unit directions, c[19][3] velocities, w[19], wh[19]; returns xi0 */
 double orc_lattice(int *e, double *c, double *w, double *wh);

@@ -10,7 +10,8 @@ Eq. 55, a dropped nu in the collision prefactor of Eq. 57, the wrong sign of
 the extrapolated equilibrium, n = N^0 gamma, a flipped lattice vector, tau
 without nu^2 (Eq. 41), minmod taking the larger slope (Eq. 53), and in the
 solid cells of the astrophysical run (Sec. III): no reset, a moving or a
-wrong-pressure cloud state.
+wrong-pressure cloud state; and in the basic model's lattice (Sec. II): a
+mistyped weight, doubled diagonals, swapped number weights.
 """
 import os
 import subprocess
@@ -21,7 +22,8 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "rlb_oracle.c")
 PINS = ["tests/test_oracle_lattice.py", "tests/test_oracle_equilibrium.py",
-        "tests/test_oracle_stream.py", "tests/test_oracle_step.py", "tests/test_oracle_solid.py"]
+        "tests/test_oracle_stream.py", "tests/test_oracle_step.py", "tests/test_oracle_solid.py",
+        "tests/test_oracle_basic.py"]
 
 MUTATIONS = {
     "printed_delta_plus_in_fR": ("fR -= 0.5 * orc_minmod(dm_y, dm_yp1);",
@@ -31,19 +33,24 @@ MUTATIONS = {
         "           - flux(pa[a], q[0], q[1], q[2], q[3], p->limiter);",
         "        s += flux(pa[a], q[2], q[3], q[4], q[4], p->limiter)\n"
         "           - flux(pa[a], q[1], q[2], q[3], q[4], p->limiter);"),
-    "off_diagonal_coefficient_doubled": ("const double a2 = 4.0 * P / L.m22;",
-                                         "const double a2 = 8.0 * P / L.m22;"),
-    "heq_first_order_sign": ("(L.c0_over_ct + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)",
-                             "(L.c0_over_ct - 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)"),
+    "off_diagonal_coefficient_doubled": ("const double a2 = 4.0 * P / L->m22;",
+                                         "const double a2 = 8.0 * P / L->m22;"),
+    "heq_first_order_sign": ("(L->c0_over_ct + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)",
+                             "(L->c0_over_ct - 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)"),
     "bulk_on_rest_population": ("if (i != 0) sf[i] += kbulk", "if (i >= 0) sf[i] += kbulk"),
-    "collision_prefactor_without_nu": ("omega = L.c0_over_ct * NU * dt / tau;",
-                                       "omega = L.c0_over_ct * dt / tau;"),
+    "collision_prefactor_without_nu": ("omega = L->c0_over_ct * NU * dt / tau;",
+                                       "omega = L->c0_over_ct * dt / tau;"),
     "extrapolation_sign": ("omega * (2.0 * feq[i] - feqp[i])", "omega * (2.0 * feqp[i] - feq[i])"),
     "density_times_gamma": ("macro[4] = mom[4] / gamma;", "macro[4] = mom[4] * gamma;"),
-    "flipped_lattice_vector": ("L.c[i][b] = 2.0 * ca * s2;",
-                               "L.c[i][b] = (i == 12 ? -2.0 : 2.0) * ca * s2;"),
+    "flipped_lattice_vector": ("l->c[i][b] = dshell * ca * s2;",
+                               "l->c[i][b] = (i == 12 ? -dshell : dshell) * ca * s2;"),
     "tau_without_nu_squared": ("return 0.5 + NU * NU * eta / (4.0 * P);",
                                "return 0.5 + eta / (4.0 * P);"),
+    "basic_diagonal_weight_typo": ("w2 = r2 * nu * nu / 1083.0;", "w2 = r2 * nu * nu / 1038.0;"),
+    "basic_diagonals_doubled": ("const double dshell = basic ? 1.0 : 2.0;",
+                                "const double dshell = basic ? 2.0 : 2.0;"),
+    "basic_number_weights_swapped": ("for (i = 1; i <= 6; ++i) l->wh[i] = 1.0 / 18.0;",
+                                     "for (i = 1; i <= 6; ++i) l->wh[i] = 1.0 / 36.0;"),
     "solid_reset_skipped": ("if (!mask[idx]) continue;", "if (mask[idx] || !mask[idx]) continue;"),
     "solid_state_moving": ("const double rest[3] = {0.0, 0.0, 0.0};", "const double rest[3] = {0.05, 0.0, 0.0};"),
     "solid_pressure_without_T": ("orc_feq(n * T, rest, fe);", "orc_feq(n, rest, fe);"),
