@@ -101,10 +101,15 @@ typedef struct {
                               * step updates one plane per class (14 population planes and 3
                               * previous-level planes instead of 38 and 5).  Results equal the
                               * 19-population step up to the rounding order of the moment sums. */
+    int model;               /* lattice: 0 the extended D3Q19 configuration (Sec. II.A, diagonals
+                              * 2 c_a, nu = sqrt(13)); 1 the basic D3Q19 lattice of Sec. II
+                              * (diagonals c_a, nu = sqrt(19) so c_a = 1, weights -44/361, 99/722,
+                              * 9/361, number weights 1/3, 1/18, 1/36).  The step is the same
+                              * (Eq. 57) on either; grids only (batched tubes: model 0). */
 } rlb_options;
 
 /* Fill *opts with the defaults: dt/dx 0.25, no overrides, viscous mode, FP64,
- * default stream, no symmetry reduction. */
+ * default stream, no symmetry reduction, the extended lattice. */
 RLB_API void rlb_default_options(rlb_options *opts);
 
 /* Validate a configuration on the host without touching the GPU.  Same
@@ -112,7 +117,7 @@ RLB_API void rlb_default_options(rlb_options *opts);
  * lattice of Sec. II.A, Eq. 42); nx, ny, nz >= 1 and N < 2^31; eta_over_s,
  * zeta_over_s >= 0; INLET only on x faces with n > 0, T > 0, |u| < 1;
  * RLB_E_UNSTABLE if dt/dx times the largest sum over moving axes of
- * |c_ia| c_0/c_t exceeds 1, or if 2 d (c_0 nu / c_t) dt alpha exceeds 1
+ * |c_ia| c_0/c_t of the chosen lattice exceeds 1, or if 2 d (c_0 nu / c_t) dt alpha exceeds 1
  * (d = number of axes with more than one cell). */
 RLB_API rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s,
                             double zeta_over_s, int limiter, const rlb_options *opts);
@@ -208,6 +213,7 @@ RLB_API const char *rlb_status_string(int status);
  * layout of rlb_get_state has plane_stride = N); out_device is a
  * caller-owned device buffer of 5 doubles, written asynchronously on
  * cuda_stream (NULL = legacy default stream).
+ * The sums take p_i = (xi0, c_i) of the extended lattice (model 0).
  * The reduction's per-block partial sums live in a fixed device array of
  * 5 x RLB_NOALLOC_MAX_BLOCKS doubles (47.5 KiB) inside the library, which
  * every GPU that loads the library holds until the process exits.  The

@@ -74,8 +74,13 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 double alpha_from(double zeta_over_s, const rlb_options &o)
 {
     if (o.alpha_override >= 0.0) return o.alpha_override;
-    return rlb::alpha_of_zeta(zeta_over_s);
+    return rlb::alpha_of_zeta(zeta_over_s, o.model);
 }
+
+// c_0/c_t, (c_0/c_t) nu and |c_ia| of a diagonal population of a lattice
+double lat_c0ct(int lat) { return lat == 1 ? rlb::Lat<1>::c0ct : rlb::Lat<0>::c0ct; }
+double lat_omegaC(int lat) { return lat == 1 ? rlb::Lat<1>::omegaC : rlb::Lat<0>::omegaC; }
+int lat_dmag(int lat) { return lat == 1 ? rlb::Lat<1>::dmag : rlb::Lat<0>::dmag; }
 
 int active_axes(const rlb_grid &g)
 {
@@ -121,20 +126,23 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.euler_mode != 0 && o.euler_mode != 1) return fail(ctx, RLB_E_INVALID, "euler_mode must be 0 or 1");
     if (o.symmetry_1d != 0)
         return fail(ctx, RLB_E_INVALID, "the 1-D symmetry reduction is available for batched tubes (rlb_batch_create)");
+    if (o.model != 0 && o.model != 1) return fail(ctx, RLB_E_INVALID, "model must be 0 (extended) or 1 (basic)");
     if (!std::isfinite(o.tau_override) || !std::isfinite(o.alpha_override))
         return fail(ctx, RLB_E_INVALID, "overrides must be finite");
     // explicit stability bounds
     const int d = active_axes(g) > 0 ? active_axes(g) : 1;
-    const double cmax = (d >= 2 ? 4.0 : 2.0) * rlb::kC0Ct;   // largest sum of |c_ia| c0/ct
+    // largest sum over the streamed axes of |c_ia| c0/ct
+    const double cmax = (d >= 2 ? 2.0 : 1.0) * lat_dmag(o.model) * lat_c0ct(o.model);
     if (o.dt_over_dx * cmax > 1.0)
-        return fail(ctx, RLB_E_UNSTABLE, "dt/dx exceeds the Courant bound of the extended lattice");
-    const double kb = rlb::kOmegaC * o.dt_over_dx * alpha_from(zeta_over_s, o);
+        return fail(ctx, RLB_E_UNSTABLE, "dt/dx exceeds the Courant bound of the lattice");
+    const double kb = lat_omegaC(o.model) * o.dt_over_dx * alpha_from(zeta_over_s, o);
     if (2.0 * d * kb > 1.0)
         return fail(ctx, RLB_E_UNSTABLE, "alpha dt exceeds the explicit diffusion bound");
     return RLB_OK;
 }
 
 // inlet ghost values: f^eq and h^eq of the inlet state
+template <int LAT>
 void inlet_ghosts(const rlb_grid &g, StepParams &sp)
 {
     const double u2 = g.inlet_u[0] * g.inlet_u[0] + g.inlet_u[1] * g.inlet_u[1] +
@@ -147,9 +155,9 @@ void inlet_ghosts(const rlb_grid &g, StepParams &sp)
     m.uz = gam * g.inlet_u[2];
     m.n = g.inlet_n;
     rlb::Coef<double> cf, ch;
-    rlb::coef_f(m, cf);
-    rlb::coef_h(m, ch);
-    const rlb::EqW<double> kf = rlb::weigh_f<double>(cf), kh = rlb::weigh_h<double>(ch);
+    rlb::coef_f<LAT>(m, cf);
+    rlb::coef_h<LAT>(m, ch);
+    const rlb::EqW<double> kf = rlb::weigh_f<double, LAT>(cf), kh = rlb::weigh_h<double, LAT>(ch);
     double *gf = sp.ghost_f, *gh = sp.ghost_h;
     [&]<int... I>(std::integer_sequence<int, I...>) {
         ((gf[I] = rlb::eq_pop<I>(kf)), ...);
@@ -189,6 +197,7 @@ void rlb_default_options(rlb_options *o)
     o->precision = RLB_FP64;
     o->cuda_stream = nullptr;
     o->symmetry_1d = 0;
+    o->model = 0;
 }
 
 rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
@@ -282,14 +291,16 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
         sp.bc_hi[a] = grid->bc_hi[a];
     }
     sp.half_lim = limiter == RLB_LIMITER_MINMOD ? 0.5 : 0.0;
-    sp.k1 = rlb::kC0Ct * o.dt_over_dx;
-    sp.k2 = 2.0 * rlb::kC0Ct * o.dt_over_dx;
-    sp.kw = rlb::kOmegaC * o.dt_over_dx;
-    sp.kbulk = rlb::kOmegaC * o.dt_over_dx * ctx->alpha;
+    sp.lat = o.model;
+    sp.k1 = lat_c0ct(o.model) * o.dt_over_dx;
+    sp.k2 = double(lat_dmag(o.model)) * lat_c0ct(o.model) * o.dt_over_dx;
+    sp.kw = lat_omegaC(o.model) * o.dt_over_dx;
+    sp.kbulk = lat_omegaC(o.model) * o.dt_over_dx * ctx->alpha;
     sp.eta_over_s = eta_over_s;
     sp.tau_override = o.tau_override;
     sp.status = ctx->d_status;
-    inlet_ghosts(*grid, sp);
+    if (o.model == 1) inlet_ghosts<1>(*grid, sp);
+    else inlet_ghosts<0>(*grid, sp);
     sp.f_k1 = float(sp.k1);
     sp.f_k2 = float(sp.k2);
     sp.f_half_lim = float(sp.half_lim);
@@ -329,7 +340,7 @@ rlb_status rlb_init(rlb_ctx *ctx, const double *n, const double *T, const double
     }
     RLB_CUDA(ctx, rlb::launch_init(ctx->fp32, ctx->N, ctx->ps, dev[0], dev[1], dev[2], dev[3], dev[4],
                                    ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur], ctx->prev, ctx->d_status,
-                                   ctx->stream));
+                                   ctx->stream, ctx->sp.lat));
     ctx->launches += 1;
     return check_device_status(ctx, RLB_E_INVALID);
 }
@@ -356,7 +367,7 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
         if (ctx->nsolid > 0) {
             RLB_CUDA(ctx, rlb::launch_solid_reset(ctx->fp32, ctx->nsolid, (const int *)((double *)ctx->solid + 3),
                                                   ctx->ps, (const double *)ctx->solid, ctx->fbuf[o], ctx->hbuf[o],
-                                                  ctx->prev, ctx->d_status, ctx->stream));
+                                                  ctx->prev, ctx->d_status, ctx->stream, ctx->sp.lat));
             ctx->launches += 1;
         }
     }
@@ -398,7 +409,7 @@ rlb_status rlb_set_solid(rlb_ctx *ctx, const unsigned char *mask, double n, doub
     const int c = ctx->cur;
     RLB_CUDA(ctx, rlb::launch_solid_reset(ctx->fp32, ctx->nsolid, (const int *)((double *)ctx->solid + 3), ctx->ps,
                                           (const double *)ctx->solid, ctx->fbuf[c], ctx->hbuf[c], ctx->prev,
-                                          ctx->d_status, ctx->stream));
+                                          ctx->d_status, ctx->stream, ctx->sp.lat));
     ctx->launches += 1;
     return check_device_status(ctx, RLB_E_INVALID);
 }
@@ -410,7 +421,7 @@ rlb_status rlb_macroscopic(rlb_ctx *ctx, double *out, int on_device)
     RLB_CUDA(ctx, cudaSetDevice(ctx->device));
     double *dst = on_device ? out : (double *)ctx->fbuf[1 - ctx->cur];   // 48 N bytes of staging
     RLB_CUDA(ctx, rlb::launch_macro(ctx->fp32, ctx->N, ctx->ps, ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur],
-                                    dst, ctx->d_status, ctx->stream));
+                                    dst, ctx->d_status, ctx->stream, ctx->sp.lat));
     ctx->launches += 1;
     if (!on_device)
         RLB_CUDA(ctx, cudaMemcpyAsync(out, dst, 6 * sizeof(double) * (size_t)ctx->N, cudaMemcpyDeviceToHost,
@@ -424,7 +435,7 @@ rlb_status rlb_conserved_totals(rlb_ctx *ctx, double *out)
     if (!out) return fail(ctx, RLB_E_INVALID, "out is NULL");
     RLB_CUDA(ctx, cudaSetDevice(ctx->device));
     RLB_CUDA(ctx, rlb::launch_totals(ctx->fp32, ctx->N, ctx->ps, ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur],
-                                     ctx->d_partial, ctx->d_tot, ctx->stream));
+                                     ctx->d_partial, ctx->d_tot, ctx->stream, ctx->sp.lat));
     ctx->launches += 2;
     RLB_CUDA(ctx, cudaMemcpyAsync(ctx->h_tot, ctx->d_tot, 5 * sizeof(double), cudaMemcpyDeviceToHost,
                                   ctx->stream));

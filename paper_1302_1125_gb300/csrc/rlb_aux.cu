@@ -1,9 +1,11 @@
 // Initialisation, macroscopic output and conserved-total kernels.
+#include <utility>
+
 #include "rlb_cellops.cuh"
 
 namespace rlb {
 
-template <typename T>
+template <typename T, int LAT>
 __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
                             const double *__restrict__ Tt, const double *__restrict__ ux,
                             const double *__restrict__ uy, const double *__restrict__ uz,
@@ -12,35 +14,35 @@ __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N) return;
-    init_cell<T>(idx, idx, ps, n, Tt, ux, uy, uz, f, h, prev, status);
+    init_cell<T, LAT>(idx, idx, ps, n, Tt, ux, uy, uz, f, h, prev, status);
 }
 
 // moments + recovery of the current populations: n, e, u_x, u_y, u_z, gamma
-template <typename T>
+template <typename T, int LAT>
 __global__ void macro_kernel(int N, long long ps, const T *__restrict__ f,
                              const T *__restrict__ h, double *__restrict__ out,
                              unsigned *status)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N) return;
-    macro_cell<T>(idx, ps, f, h, out, idx, N, status);
+    macro_cell<T, LAT>(idx, ps, f, h, out, idx, N, status);
 }
 
 // solid cells: the equilibrium of st = {n, T, 0} (the same code as the
 // initialisation, so a solid cell holds what rlb_init writes for that state)
-template <typename T>
+template <typename T, int LAT>
 __global__ void solid_reset_kernel(int M, const int *__restrict__ idx, long long ps, const double *__restrict__ st,
                                    T *__restrict__ f, T *__restrict__ h, T *__restrict__ prev, unsigned *status)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
-    init_cell<T>(0, idx[j], ps, st, st + 1, st + 2, st + 2, st + 2, f, h, prev, status);
+    init_cell<T, LAT>(0, idx[j], ps, st, st + 1, st + 2, st + 2, st + 2, f, h, prev, status);
 }
 
 // per-block partial sums of (T^00, T^0x, T^0y, T^0z, N^0); fixed grid and
 // fixed reduction order, so the result is deterministic
 constexpr int kTotBlock = 256;
-template <typename T>
+template <typename T, int LAT>
 __global__ void __launch_bounds__(kTotBlock) totals_kernel(int N, long long ps,
                                                            const T *__restrict__ f,
                                                            const T *__restrict__ h,
@@ -51,11 +53,11 @@ __global__ void __launch_bounds__(kTotBlock) totals_kernel(int N, long long ps,
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             const double fv = double(f[I * ps + idx]);
-            acc[0] += kXi0Sq * fv;
-            if constexpr (cdir<I, 0>() != 0) acc[1] += kXi0 * double(cdir<I, 0>()) * fv;
-            if constexpr (cdir<I, 1>() != 0) acc[2] += kXi0 * double(cdir<I, 1>()) * fv;
-            if constexpr (cdir<I, 2>() != 0) acc[3] += kXi0 * double(cdir<I, 2>()) * fv;
-            acc[4] += kXi0 * double(h[I * ps + idx]);
+            acc[0] += Lat<LAT>::xi0sq * fv;
+            if constexpr (cdir<I, 0, LAT>() != 0) acc[1] += Lat<LAT>::xi0 * double(cdir<I, 0, LAT>()) * fv;
+            if constexpr (cdir<I, 1, LAT>() != 0) acc[2] += Lat<LAT>::xi0 * double(cdir<I, 1, LAT>()) * fv;
+            if constexpr (cdir<I, 2, LAT>() != 0) acc[3] += Lat<LAT>::xi0 * double(cdir<I, 2, LAT>()) * fv;
+            acc[4] += Lat<LAT>::xi0 * double(h[I * ps + idx]);
         });
     }
     __shared__ double sm[5][kTotBlock / 32];
@@ -87,39 +89,55 @@ __global__ void totals_finish(int nblocks, const double *__restrict__ partial, d
 
 cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const double *T,
                         const double *ux, const double *uy, const double *uz, void *f, void *h,
-                        void *prev, unsigned *status, cudaStream_t s)
+                        void *prev, unsigned *status, cudaStream_t s, int lat)
 {
     const int b = 128, g = (N + b - 1) / b;
-    if (fp32)
-        init_kernel<float><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (float *)f, (float *)h,
-                                           (float *)prev, status);
-    else
-        init_kernel<double><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (double *)f, (double *)h,
-                                            (double *)prev, status);
+    auto go = [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (fp32)
+            init_kernel<float, L><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (float *)f, (float *)h,
+                                                  (float *)prev, status);
+        else
+            init_kernel<double, L><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (double *)f, (double *)h,
+                                                   (double *)prev, status);
+    };
+    if (lat == 1) go(std::integral_constant<int, 1>{});
+    else go(std::integral_constant<int, 0>{});
     return cudaGetLastError();
 }
 
 cudaError_t launch_macro(int fp32, int N, long long ps, const void *f, const void *h, double *out,
-                         unsigned *status, cudaStream_t s)
+                         unsigned *status, cudaStream_t s, int lat)
 {
     const int b = 128, g = (N + b - 1) / b;
-    if (fp32)
-        macro_kernel<float><<<g, b, 0, s>>>(N, ps, (const float *)f, (const float *)h, out, status);
-    else
-        macro_kernel<double><<<g, b, 0, s>>>(N, ps, (const double *)f, (const double *)h, out,
-                                             status);
+    auto go = [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (fp32)
+            macro_kernel<float, L><<<g, b, 0, s>>>(N, ps, (const float *)f, (const float *)h, out, status);
+        else
+            macro_kernel<double, L><<<g, b, 0, s>>>(N, ps, (const double *)f, (const double *)h, out,
+                                                    status);
+    };
+    if (lat == 1) go(std::integral_constant<int, 1>{});
+    else go(std::integral_constant<int, 0>{});
     return cudaGetLastError();
 }
 
 cudaError_t launch_solid_reset(int fp32, int M, const int *idx, long long ps, const double *st, void *f,
-                               void *h, void *prev, unsigned *status, cudaStream_t s)
+                               void *h, void *prev, unsigned *status, cudaStream_t s, int lat)
 {
     const int b = 128, g = (M + b - 1) / b;
-    if (fp32)
-        solid_reset_kernel<float><<<g, b, 0, s>>>(M, idx, ps, st, (float *)f, (float *)h, (float *)prev, status);
-    else
-        solid_reset_kernel<double><<<g, b, 0, s>>>(M, idx, ps, st, (double *)f, (double *)h, (double *)prev,
-                                                   status);
+    auto go = [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (fp32)
+            solid_reset_kernel<float, L><<<g, b, 0, s>>>(M, idx, ps, st, (float *)f, (float *)h, (float *)prev,
+                                                         status);
+        else
+            solid_reset_kernel<double, L><<<g, b, 0, s>>>(M, idx, ps, st, (double *)f, (double *)h,
+                                                          (double *)prev, status);
+    };
+    if (lat == 1) go(std::integral_constant<int, 1>{});
+    else go(std::integral_constant<int, 0>{});
     return cudaGetLastError();
 }
 
@@ -130,15 +148,19 @@ int totals_blocks(int N)
 }
 
 cudaError_t launch_totals(int fp32, int N, long long ps, const void *f, const void *h,
-                          double *partial, double *out, cudaStream_t s)
+                          double *partial, double *out, cudaStream_t s, int lat)
 {
     const int nb = totals_blocks(N);
-    if (fp32)
-        totals_kernel<float><<<nb, kTotBlock, 0, s>>>(N, ps, (const float *)f, (const float *)h,
-                                                      partial);
-    else
-        totals_kernel<double><<<nb, kTotBlock, 0, s>>>(N, ps, (const double *)f, (const double *)h,
-                                                       partial);
+    auto go = [&](auto lc) {
+        constexpr int L = decltype(lc)::value;
+        if (fp32)
+            totals_kernel<float, L><<<nb, kTotBlock, 0, s>>>(N, ps, (const float *)f, (const float *)h, partial);
+        else
+            totals_kernel<double, L><<<nb, kTotBlock, 0, s>>>(N, ps, (const double *)f, (const double *)h,
+                                                             partial);
+    };
+    if (lat == 1) go(std::integral_constant<int, 1>{});
+    else go(std::integral_constant<int, 0>{});
     totals_finish<<<1, 32, 0, s>>>(nb, partial, out);
     return cudaGetLastError();
 }

@@ -8,7 +8,7 @@ namespace rlb {
 
 // f = f^eq(P = nT, u), h = h^eq(n, u), previous level = this state, for the
 // input cell `in` stored at plane index `idx`
-template <typename T>
+template <typename T, int LAT = 0>
 __device__ __forceinline__ void init_cell(long long in, long long idx, long long ps, const double *__restrict__ n,
                                           const double *__restrict__ Tt, const double *__restrict__ ux,
                                           const double *__restrict__ uy, const double *__restrict__ uz,
@@ -27,10 +27,10 @@ __device__ __forceinline__ void init_cell(long long in, long long idx, long long
     m.uz = g * vz;
     m.n = n[in];
     Coef<double> a;
-    coef_f(m, a);
-    const EqW<T> kf = weigh_f<T>(a);
-    coef_h(m, a);
-    const EqW<T> kh = weigh_h<T>(a);
+    coef_f<LAT>(m, a);
+    const EqW<T> kf = weigh_f<T, LAT>(a);
+    coef_h<LAT>(m, a);
+    const EqW<T> kh = weigh_h<T, LAT>(a);
     double S = 0.0, Vx = 0.0, Vy = 0.0, Vz = 0.0, Sh = 0.0;
     for_pops(RLB_POPS, [&](auto ic) {
         constexpr int I = decltype(ic)::value;
@@ -39,9 +39,9 @@ __device__ __forceinline__ void init_cell(long long in, long long idx, long long
         h[I * ps + idx] = hv;
         S += double(fv);
         Sh += double(hv);
-        if constexpr (cdir<I, 0>() != 0) Vx += double(cdir<I, 0>()) * double(fv);
-        if constexpr (cdir<I, 1>() != 0) Vy += double(cdir<I, 1>()) * double(fv);
-        if constexpr (cdir<I, 2>() != 0) Vz += double(cdir<I, 2>()) * double(fv);
+        if constexpr (cdir<I, 0, LAT>() != 0) Vx += double(cdir<I, 0, LAT>()) * double(fv);
+        if constexpr (cdir<I, 1, LAT>() != 0) Vy += double(cdir<I, 1, LAT>()) * double(fv);
+        if constexpr (cdir<I, 2, LAT>() != 0) Vz += double(cdir<I, 2, LAT>()) * double(fv);
     });
     if constexpr (sizeof(T) == 4) {
         // FP32-storage form: the previous level is the raw moment sums
@@ -61,7 +61,7 @@ __device__ __forceinline__ void init_cell(long long in, long long idx, long long
 
 // moments + recovery of the populations at plane index `idx`: n, e, u_x,
 // u_y, u_z, gamma written to out[k * ostride + o]
-template <typename T>
+template <typename T, int LAT = 0>
 __device__ __forceinline__ void macro_cell(long long idx, long long ps, const T *__restrict__ f,
                                            const T *__restrict__ h, double *__restrict__ out, long long o,
                                            long long ostride, unsigned *status)
@@ -72,12 +72,13 @@ __device__ __forceinline__ void macro_cell(long long idx, long long ps, const T 
         const double fv = double(f[I * ps + idx]);
         sf += fv;
         sh += double(h[I * ps + idx]);
-        if constexpr (cdir<I, 0>() != 0) mx += double(cdir<I, 0>()) * fv;
-        if constexpr (cdir<I, 1>() != 0) my += double(cdir<I, 1>()) * fv;
-        if constexpr (cdir<I, 2>() != 0) mz += double(cdir<I, 2>()) * fv;
+        if constexpr (cdir<I, 0, LAT>() != 0) mx += double(cdir<I, 0, LAT>()) * fv;
+        if constexpr (cdir<I, 1, LAT>() != 0) my += double(cdir<I, 1, LAT>()) * fv;
+        if constexpr (cdir<I, 2, LAT>() != 0) mz += double(cdir<I, 2, LAT>()) * fv;
     });
     Macro m;
-    if (!recover(kXi0Sq * sf, kXi0 * mx, kXi0 * my, kXi0 * mz, kXi0 * sh, m))
+    if (!recover(Lat<LAT>::xi0sq * sf, Lat<LAT>::xi0 * mx, Lat<LAT>::xi0 * my, Lat<LAT>::xi0 * mz,
+                 Lat<LAT>::xi0 * sh, m))
         atomicOr(status, unsigned(ST_NONPHYSICAL));
     const double g = sqrt(1.0 + m.ux * m.ux + m.uy * m.uy + m.uz * m.uz);
     out[0 * ostride + o] = m.n;

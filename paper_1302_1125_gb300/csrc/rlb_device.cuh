@@ -4,7 +4,9 @@
 // equilibria, relaxation time, minmod streaming.
 //
 // Lattice units: delta x = 1, c = k_B = 1, nu = sqrt(13) so c_a = 1 and the
-// lattice velocities are the integer vectors of Eq. 42.
+// lattice velocities are the integer vectors of Eq. 42 (LAT = 0); the basic
+// D3Q19 lattice of Sec. II (LAT = 1) has nu = sqrt(19), c_a = 1 and unit
+// diagonals.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -23,15 +25,17 @@ constexpr Dir kDir[19] = {{0, 0, 0},   {1, 0, 0},   {-1, 0, 0},  {0, 1, 0},   {0
                           {-2, -2, 0}, {2, 0, 2},   {2, 0, -2},  {-2, 0, 2},  {-2, 0, -2},
                           {0, 2, 2},   {0, 2, -2},  {0, -2, 2},  {0, -2, -2}};
 
-template <int I, int A>
-__host__ __device__ constexpr int cdir()
-{
-    return A == 0 ? kDir[I].x : (A == 1 ? kDir[I].y : kDir[I].z);
-}
 template <int I>
 __host__ __device__ constexpr int shell()
 {
     return I == 0 ? 0 : (I <= 6 ? 1 : 2);
+}
+// component A of c_i on lattice LAT (the basic lattice's diagonals are c_a,
+// half the extended lattice's 2 c_a)
+template <int I, int A, int LAT = 0>
+__host__ __device__ constexpr int cdir()
+{
+    return (A == 0 ? kDir[I].x : (A == 1 ? kDir[I].y : kDir[I].z)) / (LAT == 1 && shell<I>() == 2 ? 2 : 1);
 }
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INLET = 2 };
@@ -67,12 +71,13 @@ __host__ __device__ __forceinline__ bool recover(double E, double Mx, double My,
 
 // tau from eta/s (Eq. 41 with s = n (4 - ln lambda), lambda = n / n_eq,
 // n_eq = 16 T^3 / pi^2, T = P/n, Sec. III): tau = 1/2 + nu^2 (eta/s)(4 - ln lambda)/(4 T)
+template <int LAT = 0>
 __device__ __forceinline__ double tau_of(double P, double n, double eta_over_s)
 {
     const double T = P / n;
     const double lam = n * kPi2Over16 / (T * T * T);
     const double sfac = fmax(4.0 - log(lam), kSMin);
-    return 0.5 + 13.0 * eta_over_s * sfac / (4.0 * T);
+    return 0.5 + Lat<LAT>::nu2 * eta_over_s * sfac / (4.0 * T);
 }
 
 // ---------------------------------------------------------------------------
@@ -91,14 +96,15 @@ struct Coef {
     R K0, Kb[3], Kd[3], Ko[3];   // Ko order: xy, xz, yz
 };
 
+template <int LAT = 0>
 __host__ __device__ __forceinline__ void coef_f(const Macro &m, Coef<double> &k)
 {
     const double u2 = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
     const double g = sqrt(1.0 + u2);
-    const double A = m.P * (13.0 / 9.0);
-    const double b = A * kFourOverXi0 * g;
-    const double d = A * (52.0 / 15.0);
-    const double o = A * 13.0;
+    const double A = m.P * Lat<LAT>::inv_sigma2;
+    const double b = A * Lat<LAT>::four_over_xi0 * g;
+    const double d = A * Lat<LAT>::a3f;
+    const double o = A * Lat<LAT>::a2f;
     k.K0 = A * (1.0 - (16.0 / 15.0) * u2);
     k.Kb[0] = b * m.ux;
     k.Kb[1] = b * m.uy;
@@ -111,6 +117,7 @@ __host__ __device__ __forceinline__ void coef_f(const Macro &m, Coef<double> &k)
     k.Ko[2] = o * m.uy * m.uz;
 }
 
+template <int LAT = 0>
 __host__ __device__ __forceinline__ void coef_h(const Macro &m, Coef<double> &k)
 {
     const double u2p = m.ux * m.ux + m.uy * m.uy + m.uz * m.uz;
@@ -118,7 +125,7 @@ __host__ __device__ __forceinline__ void coef_h(const Macro &m, Coef<double> &k)
     const double ig = 1.0 / g;
     const double ux = m.ux * ig, uy = m.uy * ig, uz = m.uz * ig;
     const double B = m.n * g;
-    k.K0 = B * (kC0Ct - 1.5 * (ux * ux + uy * uy + uz * uz));
+    k.K0 = B * (Lat<LAT>::c0ct - 1.5 * (ux * ux + uy * uy + uz * uz));
     k.Kb[0] = 3.0 * B * ux;
     k.Kb[1] = 3.0 * B * uy;
     k.Kb[2] = 3.0 * B * uz;
@@ -130,8 +137,9 @@ __host__ __device__ __forceinline__ void coef_h(const Macro &m, Coef<double> &k)
     k.Ko[2] = 9.0 * B * uy * uz;
 }
 
-// An equilibrium with the lattice weights and the diagonal factors 2 and 4
-// folded into its coefficients in double precision, so that a float form
+// An equilibrium with the lattice weights and the diagonal factors (2 and 4
+// on the extended lattice, 1 on the basic one) folded into its coefficients
+// in double precision, so that a float form
 // rounds each coefficient once instead of carrying a fixed rounding of the
 // weights into every population (that fixed rounding would bias the moment
 // sums, and so the conserved totals, the same way at every step).
@@ -142,7 +150,8 @@ struct EqW {
     R d0, db[3], dd[3], dk[3];     // diagonal: w2 K0, 2 w2 Kb, 4 w2 Kd, 4 w2 Ko
 };
 
-template <typename R>
+// DM = |c_ia| of a diagonal population (2 extended, 1 basic)
+template <typename R, int DM = 2>
 __host__ __device__ __forceinline__ EqW<R> weigh(const Coef<double> &k, double w0, double w1,
                                                  double w2)
 {
@@ -154,21 +163,21 @@ __host__ __device__ __forceinline__ EqW<R> weigh(const Coef<double> &k, double w
     for (int j = 0; j < 3; ++j) {
         e.ab[j] = R(w1 * k.Kb[j]);
         e.ad[j] = R(w1 * k.Kd[j]);
-        e.db[j] = R(2.0 * w2 * k.Kb[j]);
-        e.dd[j] = R(4.0 * w2 * k.Kd[j]);
-        e.dk[j] = R(4.0 * w2 * k.Ko[j]);
+        e.db[j] = R(double(DM) * w2 * k.Kb[j]);
+        e.dd[j] = R(double(DM * DM) * w2 * k.Kd[j]);
+        e.dk[j] = R(double(DM * DM) * w2 * k.Ko[j]);
     }
     return e;
 }
-template <typename R>
+template <typename R, int LAT = 0>
 __host__ __device__ __forceinline__ EqW<R> weigh_f(const Coef<double> &k)
 {
-    return weigh<R>(k, kW0, kW1, kW2);
+    return weigh<R, Lat<LAT>::dmag>(k, Lat<LAT>::w0, Lat<LAT>::w1, Lat<LAT>::w2);
 }
-template <typename R>
+template <typename R, int LAT = 0>
 __host__ __device__ __forceinline__ EqW<R> weigh_h(const Coef<double> &k)
 {
-    return weigh<R>(k, kWh0, kWh1, kWh2);
+    return weigh<R, Lat<LAT>::dmag>(k, Lat<LAT>::wh0, Lat<LAT>::wh1, Lat<LAT>::wh2);
 }
 
 // 2 k(t) - k(t - dt), the extrapolated equilibrium of Eq. 57

@@ -19,12 +19,15 @@ struct StepParams {
     double tau_override;     // > 0: fixed tau
     double ghost_f[19], ghost_h[19];   // inlet equilibria
     unsigned *status;        // device status word (bit 0: non-physical cell)
+    int lat;                 // lattice: 0 extended (Sec. II.A), 1 basic (Sec. II)
     // float copies for the FP32-storage kernel (no FP64 conversion on device)
     float f_k1, f_k2, f_half_lim, f_kw, f_kbulk, f_eta_over_s, f_tau_override;
     float f_ghost_f[19], f_ghost_h[19];
 };
 
-// launchers (kernel translation units); dim = 1, 2 or 3, euler = 0/1
+// launchers (kernel translation units); dim = 1, 2 or 3, euler = 0/1; the
+// step kernels take the lattice from p.lat, the others from lat (0 extended,
+// 1 basic)
 cudaError_t launch_step_f64(const StepParams &p, int dim, int euler, const double *f, const double *h,
                             double *fo, double *ho, double *prev, cudaStream_t s);
 cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f, const float *h,
@@ -32,18 +35,18 @@ cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float
 
 cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const double *T,
                         const double *ux, const double *uy, const double *uz, void *f, void *h,
-                        void *prev, unsigned *status, cudaStream_t s);
+                        void *prev, unsigned *status, cudaStream_t s, int lat = 0);
 cudaError_t launch_macro(int fp32, int N, long long ps, const void *f, const void *h, double *out,
-                         unsigned *status, cudaStream_t s);
+                         unsigned *status, cudaStream_t s, int lat = 0);
 // partial holds 5 * totals_blocks(N) doubles; out 5 doubles (device)
 int totals_blocks(int N);
 cudaError_t launch_totals(int fp32, int N, long long ps, const void *f, const void *h,
-                          double *partial, double *out, cudaStream_t s);
+                          double *partial, double *out, cudaStream_t s, int lat = 0);
 
 // solid cells: the M cells idx[0..M) are set to the equilibrium of the
 // state st = {n, T, 0} (device doubles) in f, h and the previous level
 cudaError_t launch_solid_reset(int fp32, int M, const int *idx, long long ps, const double *st, void *f,
-                               void *h, void *prev, unsigned *status, cudaStream_t s);
+                               void *h, void *prev, unsigned *status, cudaStream_t s, int lat = 0);
 
 // set the text rlb_last_error(NULL) returns on this thread
 void set_thread_error(const char *msg);

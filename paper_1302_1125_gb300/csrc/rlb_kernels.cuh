@@ -39,11 +39,11 @@ __device__ __forceinline__ T nbr(const T *q, int idx, const AxisNbr &a, int k, T
 // Streaming increment of one population along axis A: minus dt (c0/ct) times
 // the conservative minmod flux difference h^a(x) - h^a(x - e_a) (Eqs. 47-53),
 // and, for f with i != 0, the central second difference for the bulk term.
-template <typename T, bool IS_F, int I, int A>
+template <typename T, bool IS_F, int I, int A, int LAT>
 __device__ __forceinline__ void axis_terms(const T *q, int idx, const AxisNbr &an, T qc, T ghost,
                                            T k1, T k2, T hl, T &inc, T &lap)
 {
-    constexpr int c = cdir<I, A>();
+    constexpr int c = cdir<I, A, LAT>();
     constexpr bool need_lap = IS_F && I != 0;
     if constexpr (c > 0) {
         const T qm2 = nbr(q, idx, an, 0, ghost);
@@ -69,14 +69,14 @@ __device__ __forceinline__ void axis_terms(const T *q, int idx, const AxisNbr &a
 }
 
 // f + streaming (+ bulk) for population I: the explicit part of Eq. 57
-template <typename T, int DIM, bool IS_F, int I>
+template <typename T, int DIM, bool IS_F, int I, int LAT>
 __device__ __forceinline__ T streamed(const T *q, int idx, const AxisNbr (&am)[3], T qc, T ghost,
                                       T k1, T k2, T hl, T kbulk)
 {
     T inc = T(0), lap = T(0);
-    axis_terms<T, IS_F, I, 0>(q, idx, am[0], qc, ghost, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 1) axis_terms<T, IS_F, I, 1>(q, idx, am[1], qc, ghost, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 2) axis_terms<T, IS_F, I, 2>(q, idx, am[2], qc, ghost, k1, k2, hl, inc, lap);
+    axis_terms<T, IS_F, I, 0, LAT>(q, idx, am[0], qc, ghost, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 1) axis_terms<T, IS_F, I, 1, LAT>(q, idx, am[1], qc, ghost, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 2) axis_terms<T, IS_F, I, 2, LAT>(q, idx, am[2], qc, ghost, k1, k2, hl, inc, lap);
     if constexpr (IS_F && I != 0) inc += kbulk * lap;
     return qc + inc;
 }
@@ -87,7 +87,7 @@ __device__ __forceinline__ void flag(const StepParams &p, unsigned bits)
     atomicOr(p.status, bits);
 }
 
-template <typename T, int DIM, bool EULER>
+template <typename T, int DIM, bool EULER, int LAT>
 __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *__restrict__ f,
                                                    const T *__restrict__ h, T *__restrict__ fo,
                                                    T *__restrict__ ho, T *__restrict__ prev)
@@ -117,14 +117,14 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
             const double fv = double(fl[I]);
             sf += fv;
             sh += double(hq[I]);
-            if constexpr (cdir<I, 0>() != 0) mx += double(cdir<I, 0>()) * fv;
-            if constexpr (cdir<I, 1>() != 0) my += double(cdir<I, 1>()) * fv;
-            if constexpr (cdir<I, 2>() != 0) mz += double(cdir<I, 2>()) * fv;
+            if constexpr (cdir<I, 0, LAT>() != 0) mx += double(cdir<I, 0, LAT>()) * fv;
+            if constexpr (cdir<I, 1, LAT>() != 0) my += double(cdir<I, 1, LAT>()) * fv;
+            if constexpr (cdir<I, 2, LAT>() != 0) mz += double(cdir<I, 2, LAT>()) * fv;
         });
         Macro mt;
-        const bool ok = recover(kXi0Sq * sf, kXi0 * mx, kXi0 * my, kXi0 * mz, kXi0 * sh, mt);
+        const bool ok = recover(Lat<LAT>::xi0sq * sf, Lat<LAT>::xi0 * mx, Lat<LAT>::xi0 * my, Lat<LAT>::xi0 * mz, Lat<LAT>::xi0 * sh, mt);
         if (!ok) flag<T>(p, ST_NONPHYSICAL);
-        const double tau = p.tau_override > 0.0 ? p.tau_override : tau_of(mt.P, mt.n, p.eta_over_s);
+        const double tau = p.tau_override > 0.0 ? p.tau_override : tau_of<LAT>(mt.P, mt.n, p.eta_over_s);
         const double omega = p.kw / tau;
         // f(t+dt) = pre + kappa (G - pre), kappa = omega / (1 + omega): Eq. 57
         // solved for f(t+dt), in the form whose rounding does not scale the
@@ -138,22 +138,22 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
         mp.uz = double(prev[3 * ps + idx]);
         mp.n = double(prev[4 * ps + idx]);
         Coef<double> a, b;
-        coef_f(mt, a);
-        coef_f(mp, b);
-        const EqW<T> kf = weigh_f<T>(extrapolate(a, b));
-        coef_h(mt, a);
-        coef_h(mp, b);
-        const EqW<T> kh = weigh_h<T>(extrapolate(a, b));
+        coef_f<LAT>(mt, a);
+        coef_f<LAT>(mp, b);
+        const EqW<T> kf = weigh_f<T, LAT>(extrapolate(a, b));
+        coef_h<LAT>(mt, a);
+        coef_h<LAT>(mp, b);
+        const EqW<T> kh = weigh_h<T, LAT>(extrapolate(a, b));
 
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            const T pre = streamed<T, DIM, true, I>(f + I * ps, idx, am, fl[I], T(p.ghost_f[I]), k1,
+            const T pre = streamed<T, DIM, true, I, LAT>(f + I * ps, idx, am, fl[I], T(p.ghost_f[I]), k1,
                                                     k2, hl, kbulk);
             fo[I * ps + idx] = pre + kap * (eq_pop<I>(kf) - pre);
         });
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
-            const T pre = streamed<T, DIM, false, I>(h + I * ps, idx, am, hq[I], T(p.ghost_h[I]),
+            const T pre = streamed<T, DIM, false, I, LAT>(h + I * ps, idx, am, hq[I], T(p.ghost_h[I]),
                                                      k1, k2, hl, kbulk);
             ho[I * ps + idx] = pre + kap * (eq_pop<I>(kh) - pre);
         });
@@ -168,24 +168,24 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             const T qc = ldg(f + I * ps + idx);
-            const double fv = double(streamed<T, DIM, true, I>(f + I * ps, idx, am, qc,
+            const double fv = double(streamed<T, DIM, true, I, LAT>(f + I * ps, idx, am, qc,
                                                                T(p.ghost_f[I]), k1, k2, hl, kbulk));
             sf += fv;
-            if constexpr (cdir<I, 0>() != 0) mx += double(cdir<I, 0>()) * fv;
-            if constexpr (cdir<I, 1>() != 0) my += double(cdir<I, 1>()) * fv;
-            if constexpr (cdir<I, 2>() != 0) mz += double(cdir<I, 2>()) * fv;
+            if constexpr (cdir<I, 0, LAT>() != 0) mx += double(cdir<I, 0, LAT>()) * fv;
+            if constexpr (cdir<I, 1, LAT>() != 0) my += double(cdir<I, 1, LAT>()) * fv;
+            if constexpr (cdir<I, 2, LAT>() != 0) mz += double(cdir<I, 2, LAT>()) * fv;
             const T qh = ldg(h + I * ps + idx);
-            sh += double(streamed<T, DIM, false, I>(h + I * ps, idx, am, qh, T(p.ghost_h[I]), k1, k2,
+            sh += double(streamed<T, DIM, false, I, LAT>(h + I * ps, idx, am, qh, T(p.ghost_h[I]), k1, k2,
                                                     hl, kbulk));
         });
         Macro mt;
-        const bool ok = recover(kXi0Sq * sf, kXi0 * mx, kXi0 * my, kXi0 * mz, kXi0 * sh, mt);
+        const bool ok = recover(Lat<LAT>::xi0sq * sf, Lat<LAT>::xi0 * mx, Lat<LAT>::xi0 * my, Lat<LAT>::xi0 * mz, Lat<LAT>::xi0 * sh, mt);
         if (!ok) flag<T>(p, ST_NONPHYSICAL);
         Coef<double> a;
-        coef_f(mt, a);
-        const EqW<T> kf = weigh_f<T>(a);
-        coef_h(mt, a);
-        const EqW<T> kh = weigh_h<T>(a);
+        coef_f<LAT>(mt, a);
+        const EqW<T> kf = weigh_f<T, LAT>(a);
+        coef_h<LAT>(mt, a);
+        const EqW<T> kh = weigh_h<T, LAT>(a);
         for_pops(RLB_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             fo[I * ps + idx] = eq_pop<I>(kf);

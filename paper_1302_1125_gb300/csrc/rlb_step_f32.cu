@@ -5,7 +5,7 @@
 
 namespace rlb {
 
-template <int DIM, bool EULER, bool VEC2>
+template <int DIM, bool EULER, bool VEC2, int LAT>
 static cudaError_t launch_f32(const StepParams &p, const float *f, const float *h, float *fo, float *ho,
                              float *prev, cudaStream_t s)
 {
@@ -23,34 +23,42 @@ static cudaError_t launch_f32(const StepParams &p, const float *f, const float *
     const size_t smem = f32::step_smem_bytes(int(block.x * block.y), f32::kStageOn && VEC2 && !EULER, DIM);
     static bool attr_set = false;   // per instantiation
     if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2>,
+        const cudaError_t e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2, LAT>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    f32::step_f32_kernel<DIM, EULER, VEC2><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev);
+    f32::step_f32_kernel<DIM, EULER, VEC2, LAT><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev);
     return cudaGetLastError();
 }
 
-template <bool EULER, bool VEC2>
+template <bool EULER, bool VEC2, int LAT>
 static cudaError_t launch_dim(const StepParams &p, int dim, const float *f, const float *h, float *fo,
                              float *ho, float *prev, cudaStream_t s)
 {
-    if (dim == 1) return launch_f32<1, EULER, VEC2>(p, f, h, fo, ho, prev, s);
-    if (dim == 2) return launch_f32<2, EULER, VEC2>(p, f, h, fo, ho, prev, s);
-    return launch_f32<3, EULER, VEC2>(p, f, h, fo, ho, prev, s);
+    if (dim == 1) return launch_f32<1, EULER, VEC2, LAT>(p, f, h, fo, ho, prev, s);
+    if (dim == 2) return launch_f32<2, EULER, VEC2, LAT>(p, f, h, fo, ho, prev, s);
+    return launch_f32<3, EULER, VEC2, LAT>(p, f, h, fo, ho, prev, s);
+}
+
+template <int LAT>
+static cudaError_t launch_lat(const StepParams &p, int dim, int euler, const float *f, const float *h,
+                              float *fo, float *ho, float *prev, cudaStream_t s)
+{
+    // pair loads are 8-byte aligned when every row starts at an even index
+    const bool vec = p.nx % 2 == 0;
+    if (euler)
+        return vec ? launch_dim<true, true, LAT>(p, dim, f, h, fo, ho, prev, s)
+                   : launch_dim<true, false, LAT>(p, dim, f, h, fo, ho, prev, s);
+    return vec ? launch_dim<false, true, LAT>(p, dim, f, h, fo, ho, prev, s)
+               : launch_dim<false, false, LAT>(p, dim, f, h, fo, ho, prev, s);
 }
 
 cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f, const float *h,
                             float *fo, float *ho, float *prev, cudaStream_t s)
 {
-    // pair loads are 8-byte aligned when every row starts at an even index
-    const bool vec = p.nx % 2 == 0;
-    if (euler)
-        return vec ? launch_dim<true, true>(p, dim, f, h, fo, ho, prev, s)
-                   : launch_dim<true, false>(p, dim, f, h, fo, ho, prev, s);
-    return vec ? launch_dim<false, true>(p, dim, f, h, fo, ho, prev, s)
-               : launch_dim<false, false>(p, dim, f, h, fo, ho, prev, s);
+    if (p.lat == 1) return launch_lat<1>(p, dim, euler, f, h, fo, ho, prev, s);
+    return launch_lat<0>(p, dim, euler, f, h, fo, ho, prev, s);
 }
 
 }  // namespace rlb

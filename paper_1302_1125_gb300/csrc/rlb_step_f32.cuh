@@ -29,9 +29,12 @@ namespace rlb {
 
 namespace f32 {
 
-// constants split into float hi + lo where a double-float value is needed
-constexpr float kXi0SqHi = float(kXi0Sq);
-constexpr float kXi0SqLo = float(kXi0Sq - double(float(kXi0Sq)));
+// xi0^2 split into float hi + lo where a double-float value is needed
+template <int LAT>
+struct Xi0Sq {
+    static constexpr float hi = float(Lat<LAT>::xi0sq);
+    static constexpr float lo = float(Lat<LAT>::xi0sq - double(float(Lat<LAT>::xi0sq)));
+};
 
 template <int... Is, typename F>
 __device__ __forceinline__ void for_pops(std::integer_sequence<int, Is...>, F &&fn)
@@ -202,20 +205,22 @@ struct W2 {
 };
 
 // K0, Kb, Kd, Ko of the f equilibrium (see rlb_device.cuh) for a pair
+template <int LAT>
 __device__ __forceinline__ void coef_f2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (&Kd)[3], f2 (&Ko)[3])
 {
     const f2 u2 = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
     const f2 g = f2{sqrtf(1.0f + u2.x), sqrtf(1.0f + u2.y)};
-    const f2 A = m.P * bc(13.0f / 9.0f);
+    const f2 A = m.P * bc(Lat<LAT>::f_inv_sigma2);
     K0 = A * fma2(bc(-16.0f / 15.0f), u2, bc(1.0f));
-    const f2 b = A * bc(float(kFourOverXi0)) * g;
+    const f2 b = A * bc(float(Lat<LAT>::four_over_xi0)) * g;
     Kb[0] = b * m.ux; Kb[1] = b * m.uy; Kb[2] = b * m.uz;
-    const f2 d = A * bc(52.0f / 15.0f);
+    const f2 d = A * bc(Lat<LAT>::f_a3f);
     Kd[0] = d * m.ux * m.ux; Kd[1] = d * m.uy * m.uy; Kd[2] = d * m.uz * m.uz;
-    const f2 o = A * bc(13.0f);
+    const f2 o = A * bc(Lat<LAT>::f_a2f);
     Ko[0] = o * m.ux * m.uy; Ko[1] = o * m.ux * m.uz; Ko[2] = o * m.uy * m.uz;
 }
 
+template <int LAT>
 __device__ __forceinline__ void coef_h2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (&Kd)[3], f2 (&Ko)[3])
 {
     const f2 u2p = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
@@ -224,7 +229,7 @@ __device__ __forceinline__ void coef_h2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (
     const f2 ux = m.ux * ig, uy = m.uy * ig, uz = m.uz * ig;
     const f2 B = m.n * g;
     const f2 uu = fma2(ux, ux, fma2(uy, uy, uz * uz));
-    K0 = B * fma2(bc(-1.5f), uu, bc(float(kC0Ct)));
+    K0 = B * fma2(bc(-1.5f), uu, bc(float(Lat<LAT>::c0ct)));
     const f2 b3 = B * bc(3.0f);
     Kb[0] = b3 * ux; Kb[1] = b3 * uy; Kb[2] = b3 * uz;
     const f2 b45 = B * bc(4.5f);
@@ -236,6 +241,7 @@ __device__ __forceinline__ void coef_h2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (
 // weights folded in (Eqs. 43-45 or 59-60) and the lattice sums set to the
 // exact targets: T0 = sum_i G_i, Ta = sum_i c_ia G_i (only for f).  The rest
 // weight w0 enters only through the target (sum_i w_i = 1).
+template <int DM>
 __device__ __forceinline__ W2 weigh2(f2 K0, const f2 (&Kb)[3], const f2 (&Kd)[3], const f2 (&Ko)[3],
                                      float w0, float w1, float w2, f2 T0, const f2 *Ta)
 {
@@ -247,9 +253,9 @@ __device__ __forceinline__ W2 weigh2(f2 K0, const f2 (&Kb)[3], const f2 (&Kd)[3]
     for (int j = 0; j < 3; ++j) {
         e.ab[j] = bc(w1) * Kb[j];
         e.ad[j] = bc(w1) * Kd[j];
-        e.db[j] = bc(2.0f * w2) * Kb[j];
-        e.dd[j] = bc(4.0f * w2) * Kd[j];
-        e.dk[j] = bc(4.0f * w2) * Ko[j];
+        e.db[j] = bc(float(DM) * w2) * Kb[j];
+        e.dd[j] = bc(float(DM * DM) * w2) * Kd[j];
+        e.dk[j] = bc(float(DM * DM) * w2) * Ko[j];
     }
     // sum_i G_i = r0 + 6 a0 + 12 d0 + 2 sum ad + 8 sum dd: the rest coefficient
     // is the remainder that makes this equal T0, with the other terms summed
@@ -276,8 +282,8 @@ __device__ __forceinline__ W2 weigh2(f2 K0, const f2 (&Kb)[3], const f2 (&Kd)[3]
     if (Ta) {
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            // sum_i c_ia G_i = 2 ab_a + 16 db_a (16 db and the halving are exact)
-            e.ab[j] = bc(0.5f) * (Ta[j] - bc(16.0f) * e.db[j]);
+            // sum_i c_ia G_i = 2 ab_a + 8 DM db_a (8 DM db and the halving are exact)
+            e.ab[j] = bc(0.5f) * (Ta[j] - bc(float(8 * DM)) * e.db[j]);
         }
     }
     return e;
@@ -313,13 +319,15 @@ __device__ __forceinline__ f2 eq2(const W2 &e)
 // E^2 - |M|^2 = xi0^2 (xi0^2 S^2 - |V|^2) formed in double-float,
 // P = (E^2 - |M|^2) / (E + sqrt(E^2 + 3 (E^2 - |M|^2))), gamma^2 = (E + P)/(4 P),
 // u' = M / (4 P gamma), n = N^0 / gamma
+template <int LAT>
 __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 &Vy, const df2 &Vz,
                                          f2 Sh, bool &ok0, bool &ok1)
 {
+    constexpr float kXi0 = float(Lat<LAT>::xi0), kXi0Sq = float(Lat<LAT>::xi0sq);
     const df2 V2 = dadd(dadd(sq(Vx), sq(Vy)), sq(Vz));
-    const df2 Dr = dadd(dscale(sq(S), kXi0SqHi, kXi0SqLo), dneg(V2));
-    const f2 D = bc(float(kXi0Sq)) * (Dr.hi + Dr.lo);
-    const f2 E = bc(float(kXi0Sq)) * (S.hi + S.lo);
+    const df2 Dr = dadd(dscale(sq(S), Xi0Sq<LAT>::hi, Xi0Sq<LAT>::lo), dneg(V2));
+    const f2 D = bc(kXi0Sq) * (Dr.hi + Dr.lo);
+    const f2 E = bc(kXi0Sq) * (S.hi + S.lo);
     const f2 root2 = fma2(E, E, bc(3.0f) * D);
     const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
     Mac2 m;
@@ -327,11 +335,11 @@ __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 
     const f2 fourP = bc(4.0f) * m.P;
     const f2 g2 = f2{(E.x + m.P.x) / fourP.x, (E.y + m.P.y) / fourP.y};
     const f2 g = f2{sqrtf(g2.x), sqrtf(g2.y)};
-    const f2 s = f2{float(kXi0) / (fourP.x * g.x), float(kXi0) / (fourP.y * g.y)};
+    const f2 s = f2{kXi0 / (fourP.x * g.x), kXi0 / (fourP.y * g.y)};
     m.ux = (Vx.hi + Vx.lo) * s;
     m.uy = (Vy.hi + Vy.lo) * s;
     m.uz = (Vz.hi + Vz.lo) * s;
-    m.n = f2{float(kXi0) * Sh.x / g.x, float(kXi0) * Sh.y / g.y};
+    m.n = f2{kXi0 * Sh.x / g.x, kXi0 * Sh.y / g.y};
     ok0 = E.x > 0.0f && D.x > 0.0f && isfinite(m.n.x) && isfinite(s.x);
     ok1 = E.y > 0.0f && D.y > 0.0f && isfinite(m.n.y) && isfinite(s.y);
     return m;
@@ -339,10 +347,12 @@ __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 
 
 // the same recovery from plain float sums (used for the previous level, whose
 // equilibrium only shapes the non-conserved part of 2 f^eq(t) - f^eq(t - dt))
+template <int LAT>
 __device__ __forceinline__ Mac2 recover2f(f2 S, f2 Vx, f2 Vy, f2 Vz, f2 Sh)
 {
-    const f2 E = bc(float(kXi0Sq)) * S;
-    const f2 M2 = bc(float(kXi0Sq)) * fma2(Vx, Vx, fma2(Vy, Vy, Vz * Vz));
+    constexpr float kXi0 = float(Lat<LAT>::xi0), kXi0Sq = float(Lat<LAT>::xi0sq);
+    const f2 E = bc(kXi0Sq) * S;
+    const f2 M2 = bc(kXi0Sq) * fma2(Vx, Vx, fma2(Vy, Vy, Vz * Vz));
     const f2 D = fma2(E, E, -M2);
     const f2 root2 = fma2(E, E, bc(3.0f) * D);
     const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
@@ -350,30 +360,31 @@ __device__ __forceinline__ Mac2 recover2f(f2 S, f2 Vx, f2 Vy, f2 Vz, f2 Sh)
     m.P = f2{D.x / den.x, D.y / den.y};
     const f2 fourP = bc(4.0f) * m.P;
     const f2 g = f2{sqrtf((E.x + m.P.x) / fourP.x), sqrtf((E.y + m.P.y) / fourP.y)};
-    const f2 s = f2{float(kXi0) / (fourP.x * g.x), float(kXi0) / (fourP.y * g.y)};
+    const f2 s = f2{kXi0 / (fourP.x * g.x), kXi0 / (fourP.y * g.y)};
     m.ux = Vx * s;
     m.uy = Vy * s;
     m.uz = Vz * s;
-    m.n = f2{float(kXi0) * Sh.x / g.x, float(kXi0) * Sh.y / g.y};
+    m.n = f2{kXi0 * Sh.x / g.x, kXi0 * Sh.y / g.y};
     return m;
 }
 
 // tau from eta/s (Eq. 41 with the entropy of Sec. III), float
+template <int LAT>
 __device__ __forceinline__ float tau1(float P, float n, float eta_over_s)
 {
     const float T = P / n;
     const float lam = n * float(kPi2Over16) / (T * T * T);
     const float sfac = fmaxf(4.0f - logf(lam), float(kSMin));
-    return 0.5f + 13.0f * eta_over_s * sfac / (4.0f * T);
+    return 0.5f + Lat<LAT>::f_nu2 * eta_over_s * sfac / (4.0f * T);
 }
 
 // streaming increment of population I along axis A for the pair (+ bulk lap)
-template <bool IS_F, int I, int A, typename Src>
+template <bool IS_F, int I, int A, int LAT, typename Src>
 __device__ __forceinline__ void axis2(const Src &src, const Geo &g, const StepParams &p, const float (&xv)[6],
                                       f2 C, float k1, float k2, float hl, f2 &inc, f2 &lap)
 {
     constexpr int sb = 3 * A;   // first staging slot of axis A (A = 1, 2)
-    constexpr int c = cdir<I, A>();
+    constexpr int c = cdir<I, A, LAT>();
     constexpr bool need_lap = IS_F && I != 0;
     const float k = (c == 1 || c == -1) ? k1 : k2;
     if constexpr (A == 0) {
@@ -416,11 +427,11 @@ __device__ __forceinline__ void axis2(const Src &src, const Geo &g, const StepPa
 }
 
 // f (or h) + streaming (+ bulk) of population I for the pair: the explicit part of Eq. 57
-template <int DIM, bool IS_F, int I, bool VEC2, int LD, typename Src>
+template <int DIM, bool IS_F, int I, bool VEC2, int LD, int LAT, typename Src>
 __device__ __forceinline__ f2 streamed2(const Src &src, const float *q, const Geo &g, const StepParams &p,
                                         float ghost, float k1, float k2, float hl, float kb)
 {
-    constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
+    constexpr bool xneed = cdir<I, 0, LAT>() != 0 || (IS_F && I != 0);
     float xv[6];
     f2 C;
     if constexpr (xneed) {
@@ -430,9 +441,9 @@ __device__ __forceinline__ f2 streamed2(const Src &src, const float *q, const Ge
         C = src.get(1, 0);
     }
     f2 inc = bc(0.0f), lap = bc(0.0f);
-    if constexpr (xneed) axis2<IS_F, I, 0>(src, g, p, xv, C, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 1) axis2<IS_F, I, 1>(src, g, p, xv, C, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 2) axis2<IS_F, I, 2>(src, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (xneed) axis2<IS_F, I, 0, LAT>(src, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 1) axis2<IS_F, I, 1, LAT>(src, g, p, xv, C, k1, k2, hl, inc, lap);
+    if constexpr (DIM > 2) axis2<IS_F, I, 2, LAT>(src, g, p, xv, C, k1, k2, hl, inc, lap);
     if constexpr (IS_F && I != 0) inc = fma2(bc(kb), lap, inc);
     return C + inc;
 }
@@ -466,13 +477,13 @@ constexpr int kStageAhead = kStageBufs - 1;  // prefetch distance in populations
 // staging buffer J % kStageBufs: the same pairs, in the same
 // slots, that streamed2 reads through StageSrc.  dst0 = shared address of
 // slot 0 of buffer 0 of this thread, sstride = bytes between slots.
-template <int DIM, int NP, int J>
+template <int DIM, int NP, int J, int LAT>
 __device__ __forceinline__ void stage_item(const float *f, const float *h, const Geo &g, const StepParams &p,
                                            long long ps, unsigned dst0, unsigned sstride)
 {
     constexpr bool IS_F = J < NP;
     constexpr int I = rep<NP>(IS_F ? J : J - NP);
-    constexpr bool xneed = cdir<I, 0>() != 0 || (IS_F && I != 0);
+    constexpr bool xneed = cdir<I, 0, LAT>() != 0 || (IS_F && I != 0);
     constexpr bool need_lap = IS_F && I != 0;
     const float *q = (IS_F ? f : h) + I * ps + g.idx0;
     const unsigned d = dst0 + unsigned(J % kStageBufs) * stage_slots<DIM>() * sstride;
@@ -483,7 +494,7 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
     cp8(d + 1 * sstride, q);
     auto axis = [&](auto ac) {
         constexpr int A = decltype(ac)::value;
-        constexpr int c = cdir<I, A>();
+        constexpr int c = cdir<I, A, LAT>();
         const unsigned b = d + unsigned(3 * A) * sstride;
         if constexpr (c > 0) {
             cp8(b, q + off_of<A>(g, p, -2));
@@ -520,7 +531,8 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
 // NP = 7: the 1-D symmetry reduction (see rep and mult); only the planes of
 // the 7 class representatives are read and written, and the previous level's
 // planes of sum c_y f and sum c_z f (zero) are left alone.
-template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false, int NP = 19>
+template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false, int NP = 19,
+          int LAT = 0>
 __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
                                             const float *__restrict__ f, const float *__restrict__ h,
                                             float *__restrict__ fo, float *__restrict__ ho,
@@ -536,7 +548,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
     if constexpr (STAGE) {
         sdst0 = unsigned(__cvta_generic_to_shared(stage));
         for_pops(std::make_integer_sequence<int, kStageAhead>{}, [&](auto jc) {
-            stage_item<DIM, NP, decltype(jc)::value>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
+            stage_item<DIM, NP, decltype(jc)::value, LAT>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
         });
     }
     // the explicit part of item J (J < NP: f class J, else h class J - NP)
@@ -548,16 +560,16 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         const float ghost = IS_F ? p.f_ghost_f[I] : p.f_ghost_h[I];
         if constexpr (STAGE) {
             if constexpr (J + kStageAhead < NI) {
-                stage_item<DIM, NP, J + kStageAhead>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
+                stage_item<DIM, NP, J + kStageAhead, LAT>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
                 cp_wait<kStageAhead>();
             } else {
                 cp_wait<NI - 1 - J>();   // the groups issued after item J's
             }
             const StageSrc src{stage + (J % kStageBufs) * stage_slots<DIM>() * sstride, sstride};
-            return streamed2<DIM, IS_F, I, VEC2, LD>(src, q, g, p, ghost, k1, k2, hl, kb);
+            return streamed2<DIM, IS_F, I, VEC2, LD, LAT>(src, q, g, p, ghost, k1, k2, hl, kb);
         } else {
             const GlobalSrc<VEC2, LD> src{q, g};
-            return streamed2<DIM, IS_F, I, VEC2, LD>(src, q, g, p, ghost, k1, k2, hl, kb);
+            return streamed2<DIM, IS_F, I, VEC2, LD, LAT>(src, q, g, p, ghost, k1, k2, hl, kb);
         }
     };
 
@@ -575,7 +587,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                 return w == 1 ? v : (w == -1 ? -v : bc(float(w)) * v);
             };
             acc(S, scaled(std::integral_constant<int, m>{}));
-            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+            constexpr int cx = cdir<I, 0, LAT>(), cy = cdir<I, 1, LAT>(), cz = cdir<I, 2, LAT>();
             if constexpr (cx != 0) acc(Vx, scaled(std::integral_constant<int, cx * m>{}));
             if constexpr (NP == 19) {   // under the reduction sum c_y f = sum c_z f = 0
                 if constexpr (cy != 0) acc(Vy, scaled(std::integral_constant<int, cy>{}));
@@ -586,7 +598,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         });
         const f2 Sh = Hs.hi + Hs.lo;
         bool ok0, ok1;
-        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        const Mac2 mt = recover2<LAT>(S, Vx, Vy, Vz, Sh, ok0, ok1);
         if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
 
         f2 kap;
@@ -595,8 +607,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
             if (p.f_tau_override > 0.0f) {
                 t0 = t1 = p.f_tau_override;
             } else {
-                t0 = tau1(mt.P.x, mt.n.x, eos);
-                t1 = tau1(mt.P.y, mt.n.y, eos);
+                t0 = tau1<LAT>(mt.P.x, mt.n.x, eos);
+                t1 = tau1<LAT>(mt.P.y, mt.n.y, eos);
             }
             const float kw = p.f_kw;
             const float w0 = kw / t0, w1 = kw / t1;
@@ -610,7 +622,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         const f2 Vpy = NP == 19 ? ldpair<VEC2, LD>(prev + 2 * ps, g, 0) : bc(0.0f);
         const f2 Vpz = NP == 19 ? ldpair<VEC2, LD>(prev + 3 * ps, g, 0) : bc(0.0f);
         const f2 Shp = ldpair<VEC2, LD>(prev + 4 * ps, g, 0);
-        const Mac2 mp = recover2f(Sp, Vpx, Vpy, Vpz, Shp);
+        const Mac2 mp = recover2f<LAT>(Sp, Vpx, Vpy, Vpz, Shp);
         const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
         f2 Ta[3];
         Ta[0] = fma2(bc(2.0f), Vx.hi + Vx.lo, -Vpx);
@@ -622,8 +634,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         f2 H0, Hb[3], Hd[3], Ho[3];
         {
             f2 L0, Lb[3], Ld[3], Lo[3];
-            coef_h2(mt, H0, Hb, Hd, Ho);
-            coef_h2(mp, L0, Lb, Ld, Lo);
+            coef_h2<LAT>(mt, H0, Hb, Hd, Ho);
+            coef_h2<LAT>(mp, L0, Lb, Ld, Lo);
             H0 = fma2(bc(2.0f), H0, -L0);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -635,8 +647,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         f2 T0h = fma2(bc(2.0f), Sh, -Shp);
         {
             f2 K0, Kb[3], Kd[3], Ko[3], L0, Lb[3], Ld[3], Lo[3];
-            coef_f2(mt, K0, Kb, Kd, Ko);
-            coef_f2(mp, L0, Lb, Ld, Lo);
+            coef_f2<LAT>(mt, K0, Kb, Kd, Ko);
+            coef_f2<LAT>(mp, L0, Lb, Ld, Lo);
             K0 = fma2(bc(2.0f), K0, -L0);
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
@@ -644,7 +656,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                 Kd[j] = fma2(bc(2.0f), Kd[j], -Ld[j]);
                 Ko[j] = fma2(bc(2.0f), Ko[j], -Lo[j]);
             }
-            const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), T0, Ta);
+            const W2 ef = weigh2<Lat<LAT>::dmag>(K0, Kb, Kd, Ko, float(Lat<LAT>::w0), float(Lat<LAT>::w1), float(Lat<LAT>::w2), T0, Ta);
             // the raw sums of this level become the next step's previous level
             stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
             stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
@@ -681,7 +693,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                     Ho[j] = park[(7 + j) * pstride];
                 }
             }
-            const W2 eh = weigh2(H0, Hb, Hd, Ho, float(kWh0), float(kWh1), float(kWh2), T0h, nullptr);
+            const W2 eh = weigh2<Lat<LAT>::dmag>(H0, Hb, Hd, Ho, float(Lat<LAT>::wh0), float(Lat<LAT>::wh1), float(Lat<LAT>::wh2), T0h, nullptr);
             for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
                 constexpr int k = decltype(kc)::value;
                 constexpr int I = rep<NP>(k);
@@ -696,7 +708,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
             constexpr int I = decltype(ic)::value;
             const f2 v = item(std::integral_constant<int, I>{});
             acc(S, v);
-            constexpr int cx = cdir<I, 0>(), cy = cdir<I, 1>(), cz = cdir<I, 2>();
+            constexpr int cx = cdir<I, 0, LAT>(), cy = cdir<I, 1, LAT>(), cz = cdir<I, 2, LAT>();
             if constexpr (cx != 0) acc(Vx, cx > 0 ? (cx == 1 ? v : v + v) : (cx == -1 ? -v : -(v + v)));
             if constexpr (cy != 0) acc(Vy, cy > 0 ? (cy == 1 ? v : v + v) : (cy == -1 ? -v : -(v + v)));
             if constexpr (cz != 0) acc(Vz, cz > 0 ? (cz == 1 ? v : v + v) : (cz == -1 ? -v : -(v + v)));
@@ -704,14 +716,14 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         });
         const f2 Sh = Hs.hi + Hs.lo;
         bool ok0, ok1;
-        const Mac2 mt = recover2(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        const Mac2 mt = recover2<LAT>(S, Vx, Vy, Vz, Sh, ok0, ok1);
         if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
         const f2 Ta[3] = {Vx.hi + Vx.lo, Vy.hi + Vy.lo, Vz.hi + Vz.lo};
         f2 K0, Kb[3], Kd[3], Ko[3];
-        coef_f2(mt, K0, Kb, Kd, Ko);
-        const W2 ef = weigh2(K0, Kb, Kd, Ko, float(kW0), float(kW1), float(kW2), S.hi + S.lo, Ta);
-        coef_h2(mt, K0, Kb, Kd, Ko);
-        const W2 eh = weigh2(K0, Kb, Kd, Ko, float(kWh0), float(kWh1), float(kWh2), Sh, nullptr);
+        coef_f2<LAT>(mt, K0, Kb, Kd, Ko);
+        const W2 ef = weigh2<Lat<LAT>::dmag>(K0, Kb, Kd, Ko, float(Lat<LAT>::w0), float(Lat<LAT>::w1), float(Lat<LAT>::w2), S.hi + S.lo, Ta);
+        coef_h2<LAT>(mt, K0, Kb, Kd, Ko);
+        const W2 eh = weigh2<Lat<LAT>::dmag>(K0, Kb, Kd, Ko, float(Lat<LAT>::wh0), float(Lat<LAT>::wh1), float(Lat<LAT>::wh2), Sh, nullptr);
         for_pops(RLB_F32_POPS, [&](auto ic) {
             constexpr int I = decltype(ic)::value;
             stpair<VEC2>(fo + I * ps, g, eq2<I>(ef));
@@ -748,7 +760,7 @@ constexpr size_t step_smem_bytes(int nthr, bool stage, int dim)
     return sizeof(f2) * size_t(nthr) * ((kParkOn ? kParkSlots : 0) + (stage ? 3 * dim * kStageBufs : 0));
 }
 
-template <int DIM, bool EULER, bool VEC2>
+template <int DIM, bool EULER, bool VEC2, int LAT>
 __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
     step_f32_kernel(const StepParams p, const float *__restrict__ f, const float *__restrict__ h,
                     float *__restrict__ fo, float *__restrict__ ho, float *__restrict__ prev)
@@ -790,7 +802,8 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
     const int nthr = blockDim.x * blockDim.y;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     constexpr bool STAGE = kStageOn && VEC2 && !EULER;
-    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho, prev, ps,
+    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE, 19, LAT>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho,
+                                                                  prev, ps,
                                                          s_park + tid, nthr,
                                                          s_park + (kParkOn ? kParkSlots * nthr : 0) + tid, nthr);
 }

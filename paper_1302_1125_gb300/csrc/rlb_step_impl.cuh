@@ -6,7 +6,7 @@
 
 namespace rlb {
 
-template <typename T, int DIM, bool EULER>
+template <typename T, int DIM, bool EULER, int LAT>
 cudaError_t launch_step_t(const StepParams &p, const T *f, const T *h, T *fo, T *ho, T *prev,
                           cudaStream_t s)
 {
@@ -18,22 +18,30 @@ cudaError_t launch_step_t(const StepParams &p, const T *f, const T *h, T *fo, T 
         block = dim3(32, 4, 1);
         grid = dim3((p.nx + 31) / 32, (p.ny + 3) / 4, p.nz);
     }
-    step_kernel<T, DIM, EULER><<<grid, block, 0, s>>>(p, f, h, fo, ho, prev);
+    step_kernel<T, DIM, EULER, LAT><<<grid, block, 0, s>>>(p, f, h, fo, ho, prev);
     return cudaGetLastError();
+}
+
+template <typename T, int LAT>
+cudaError_t launch_step_lat(const StepParams &p, int dim, int euler, const T *f, const T *h, T *fo, T *ho,
+                            T *prev, cudaStream_t s)
+{
+    if (euler) {
+        if (dim == 1) return launch_step_t<T, 1, true, LAT>(p, f, h, fo, ho, prev, s);
+        if (dim == 2) return launch_step_t<T, 2, true, LAT>(p, f, h, fo, ho, prev, s);
+        return launch_step_t<T, 3, true, LAT>(p, f, h, fo, ho, prev, s);
+    }
+    if (dim == 1) return launch_step_t<T, 1, false, LAT>(p, f, h, fo, ho, prev, s);
+    if (dim == 2) return launch_step_t<T, 2, false, LAT>(p, f, h, fo, ho, prev, s);
+    return launch_step_t<T, 3, false, LAT>(p, f, h, fo, ho, prev, s);
 }
 
 template <typename T>
 cudaError_t launch_step_any(const StepParams &p, int dim, int euler, const T *f, const T *h, T *fo,
                             T *ho, T *prev, cudaStream_t s)
 {
-    if (euler) {
-        if (dim == 1) return launch_step_t<T, 1, true>(p, f, h, fo, ho, prev, s);
-        if (dim == 2) return launch_step_t<T, 2, true>(p, f, h, fo, ho, prev, s);
-        return launch_step_t<T, 3, true>(p, f, h, fo, ho, prev, s);
-    }
-    if (dim == 1) return launch_step_t<T, 1, false>(p, f, h, fo, ho, prev, s);
-    if (dim == 2) return launch_step_t<T, 2, false>(p, f, h, fo, ho, prev, s);
-    return launch_step_t<T, 3, false>(p, f, h, fo, ho, prev, s);
+    if (p.lat == 1) return launch_step_lat<T, 1>(p, dim, euler, f, h, fo, ho, prev, s);
+    return launch_step_lat<T, 0>(p, dim, euler, f, h, fo, ho, prev, s);
 }
 
 }  // namespace rlb

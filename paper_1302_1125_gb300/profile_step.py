@@ -41,7 +41,7 @@ def run_batch(a):
     k = max(1, full.B // a.scale)
     spec = W.batch_tubes(count=k)
     steps = np.maximum(spec.steps // a.scale, 1)
-    b = rlb.Batch.from_spec(spec)
+    b = rlb.Batch.from_spec(spec, symmetry_1d=int(a.symmetry))
     if a.tuning:
         b.set_tuning(*[int(v) for v in a.tuning.split(",")])
     b.init(*spec.fields())
@@ -70,6 +70,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--tuning", default="", help="batch launch shape threads,bound,cluster,pairs_per_thread")
+    ap.add_argument("--symmetry", action="store_true", help="batch: the 1-D symmetry reduction")
     a = ap.parse_args()
     B.build()
     if a.workload == "batch_tubes":

@@ -22,6 +22,7 @@ RLB_E_UNSTABLE, RLB_E_NONPHYSICAL, RLB_E_TIMEOUT = -4, -5, -6
 LIMITER_MINMOD, LIMITER_NONE = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_INLET = 0, 1, 2
 FP64, FP32_STORAGE = 0, 1
+MODEL_EXTENDED, MODEL_BASIC = 0, 1
 Q = 19
 
 
@@ -34,7 +35,8 @@ class rlb_grid(C.Structure):
 class rlb_options(C.Structure):
     _fields_ = [("dt_over_dx", C.c_double), ("tau_override", C.c_double),
                 ("alpha_override", C.c_double), ("euler_mode", C.c_int),
-                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("symmetry_1d", C.c_int)]
+                ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("symmetry_1d", C.c_int),
+                ("model", C.c_int)]
 
 
 class rlb_batch_tuning(C.Structure):
@@ -154,9 +156,9 @@ def make_grid(nx, ny=1, nz=1, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
 
 
 def make_options(dt_over_dx=0.25, tau_override=0.0, alpha_override=-1.0, euler_mode=0,
-                 precision=FP64, cuda_stream=None, symmetry_1d=0):
+                 precision=FP64, cuda_stream=None, symmetry_1d=0, model=MODEL_EXTENDED):
     return rlb_options(float(dt_over_dx), float(tau_override), float(alpha_override),
-                       int(euler_mode), int(precision), cuda_stream, int(symmetry_1d))
+                       int(euler_mode), int(precision), cuda_stream, int(symmetry_1d), int(model))
 
 
 def rlb_check_config(grid, Q, eta_over_s, zeta_over_s, limiter, opts) -> int:
@@ -271,13 +273,14 @@ class Grid:
                  bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
                  eta_over_s=0.1, zeta_over_s=0.0, limiter=LIMITER_MINMOD, dt_over_dx=0.25,
                  tau_override=0.0, alpha_override=-1.0, euler_mode=0, precision=FP64,
-                 stream="current"):
+                 model=MODEL_EXTENDED, stream="current"):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = int(precision)
         s = _current_stream() if stream == "current" else stream
         self._grid = make_grid(nx, ny, nz, bc_lo, bc_hi, inlet)
-        self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s)
+        self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s,
+                                  model=model)
         self.ctx = rlb_create(self._grid, Q, eta_over_s, zeta_over_s, limiter, self._opts)
 
     @classmethod

@@ -54,7 +54,8 @@ def cfg(**kw):
     for k in list(kw):
         if k in g:
             g[k] = kw.pop(k)
-        elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision", "symmetry_1d"):
+        elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision", "symmetry_1d",
+                   "model"):
             o[k] = kw.pop(k)
     return rlb.make_grid(**g), rlb.make_options(**o), kw
 
@@ -78,6 +79,11 @@ def cfg(**kw):
     ({"alpha_override": 0.5}, rlb.RLB_OK),
     ({"dt_over_dx": -1.0}, rlb.RLB_E_INVALID),
     ({"symmetry_1d": 1}, rlb.RLB_E_INVALID),     # batched tubes only
+    ({"model": 2}, rlb.RLB_E_INVALID),
+    ({"model": 1, "dt_over_dx": 1.19}, rlb.RLB_OK),        # basic lattice, 1-D: bound sqrt(27/19) = 1.192
+    ({"model": 1, "dt_over_dx": 1.2}, rlb.RLB_E_UNSTABLE),
+    ({"model": 1, "ny": 8, "dt_over_dx": 0.59}, rlb.RLB_OK),   # 2-D: unit diagonals, bound 0.596
+    ({"model": 1, "ny": 8, "dt_over_dx": 0.6}, rlb.RLB_E_UNSTABLE),
 ])
 def test_host_validation(lib, change, expect):
     change = dict(change)

@@ -1,0 +1,116 @@
+"""The basic model (rlb_options.model = 1: the D3Q19 lattice of Sec. II with
+unit diagonals) on the GPU, through the C ABI, against the oracle's basic
+model.
+
+* FP64 form within 1e-10 relative (max norm) of the oracle on a 3-D periodic
+  box and a 1-D shock tube.
+* FP32-storage form: L1 relative error against the oracle <= 1e-4, and
+  conserved-total drift <= 1e-6 over 2000 steps on a periodic box.
+* The paper's comparison (Sec. III, P ratio 32, beta ~ 0.7): the basic model
+  reports a non-physical state where the extended model runs.
+"""
+import numpy as np
+import pytest
+
+from paper_1302_1125_gb300 import rlb
+from paper_1302_1125_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+BASIC = rlb.MODEL_BASIC
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1302_1125_gb300 import build
+    build.build()
+    assert torch.cuda.is_available(), "the gpu tests need a CUDA device"
+
+
+def gpu_run(w, steps, precision, model=BASIC):
+    g = rlb.Grid(w.nx, w.ny, w.nz, bc_lo=w.bc_lo, bc_hi=w.bc_hi, eta_over_s=w.eta_over_s,
+                 zeta_over_s=w.zeta_over_s, dt_over_dx=w.dt_over_dx, tau_override=w.tau_override,
+                 alpha_override=w.alpha_override, precision=precision, model=model)
+    g.init(*[torch.as_tensor(a, device="cuda") for a in w.fields()])
+    return g
+
+
+def oracle_run(orc, w, steps, model=BASIC):
+    p = orc.Params(nx=w.nx, ny=w.ny, nz=w.nz, bc_lo=w.bc_lo, bc_hi=w.bc_hi, dt=w.dt_over_dx,
+                   eta_over_s=w.eta_over_s, zeta_over_s=w.zeta_over_s, tau_override=w.tau_override,
+                   alpha_override=w.alpha_override, model=model)
+    s = orc.init(p, *w.fields())
+    orc.step(s, steps)
+    assert s.nonphysical == 0
+    return orc.macroscopic(s)
+
+
+def relinf(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def l1rel(a, b):
+    return float(np.sum(np.abs(a - b)) / max(np.sum(np.abs(b)), 1e-300))
+
+
+def box():
+    return W.periodic_box(12, 10, 8, seed=21, tau_override=0.0, alpha_override=0.0, gamma_max=1.5,
+                          dt_over_dx=0.25)
+
+
+def tube():
+    return W.riemann_tube(400, 5.43 / 2.22, 2.0, eta_over_s=0.01, dt_over_dx=0.25)
+
+
+@pytest.mark.parametrize("make,steps", [(box, 120), (tube, 500)])
+def test_basic_fp64_matches_oracle(orc, make, steps):
+    w = make()
+    g = gpu_run(w, steps, rlb.FP64)
+    g.step(steps)
+    mg = g.macroscopic(device=False)
+    mo = oracle_run(orc, w, steps)
+    for k in range(6):
+        assert relinf(mg[k], mo[k]) <= 1e-10, (k, relinf(mg[k], mo[k]))
+    g.close()
+
+
+@pytest.mark.parametrize("make,steps", [(box, 120), (tube, 500)])
+def test_basic_fp32_l1(orc, make, steps):
+    w = make()
+    g = gpu_run(w, steps, rlb.FP32_STORAGE)
+    g.step(steps)
+    mg = g.macroscopic(device=False)
+    mo = oracle_run(orc, w, steps)
+    errs = [l1rel(mg[k], mo[k]) for k in (0, 1)]
+    errs.append(float(np.sum(np.abs(mg[2] - mo[2])) / np.sum(np.abs(mo[5]))))
+    assert max(errs) <= 1e-4, errs
+    g.close()
+
+
+# FP64: per-step rounding of the totals random-walks, ~ eps sqrt(N) sqrt(steps)
+# = 1.1e-16 x 44 x 45 ~ 2e-13 for 1920 cells and 2000 steps
+@pytest.mark.parametrize("precision,tol", [(rlb.FP64, 5e-13), (rlb.FP32_STORAGE, 1e-6)])
+def test_basic_conservation_drift(precision, tol):
+    # without the bulk term the basic model goes non-physical on this machine
+    # within ~500 steps (the oracle agrees); alpha = 0.1 keeps it physical
+    w = W.periodic_box(48, 40, 1, seed=11, tau_override=0.8, alpha_override=0.1, gamma_max=1.5,
+                       dt_over_dx=0.25)
+    g = gpu_run(w, 0, precision)
+    t0 = g.totals()
+    g.step(2000)
+    t1 = g.totals()
+    assert (np.abs(t1 - t0) / t0[0]).max() <= tol
+    g.close()
+
+
+def test_paper_basic_versus_extended_on_the_gpu():
+    w = W.riemann_tube(400, 32.0, 2.0, eta_over_s=0.01, dt_over_dx=0.25, alpha_override=0.0)
+    g = gpu_run(w, 0, rlb.FP64, BASIC)
+    with pytest.raises(rlb.RLBError) as e:
+        g.step(600)
+    assert e.value.status == rlb.RLB_E_NONPHYSICAL
+    g.close()
+    w = W.riemann_tube(400, 32.0, 2.0, eta_over_s=0.01, dt_over_dx=0.25, alpha_override=0.15)
+    g = gpu_run(w, 0, rlb.FP64, rlb.MODEL_EXTENDED)
+    g.step(600)
+    g.close()
