@@ -381,6 +381,58 @@ def sphere_run(torch, rlb, W, device_index):
     return out
 
 
+def basic_model_run(torch, rlb, W, hbm_peak):
+    """The basic model (Sec. II: D3Q19 with unit diagonals) on the headline
+    grid, and the paper's basic-versus-extended comparison (P ratio 32,
+    beta ~ 0.7, eta/s 0.01, dt/dx 0.25; alpha 0.15 for the extended model)."""
+    w = W.cloud_3d()
+    fields = [torch.as_tensor(a, device="cuda") for a in w.fields()]
+    stream = torch.cuda.current_stream()
+    out = {"workload": "cloud_3d 512x256x256 on the basic lattice (alpha 0.2, dt/dx 0.15)", "unit": UNIT}
+    for name, prec, steps in (("fp32_storage", rlb.FP32_STORAGE, 50), ("fp64", rlb.FP64, 5)):
+        g = rlb.Grid(w.nx, w.ny, w.nz, bc_lo=w.bc_lo, bc_hi=w.bc_hi, inlet=w.inlet, eta_over_s=w.eta_over_s,
+                     zeta_over_s=w.zeta_over_s, dt_over_dx=w.dt_over_dx, alpha_override=w.alpha_override,
+                     precision=prec, model=rlb.MODEL_BASIC)
+        g.init(*fields)
+        try:
+            g.step(3)
+            torch.cuda.synchronize()
+            s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            g.step(steps)
+            s1.record(stream)
+            torch.cuda.synchronize()
+        except rlb.RLBError as e:
+            out[name] = {"value": None, "status": rlb.status_string(e.status)}
+            g.close()
+            continue
+        ms = s0.elapsed_time(s1) / steps
+        bytes_ = BYTES_FP32 if prec == rlb.FP32_STORAGE else BYTES_FP64
+        out[name] = {"value": w.N / (ms * 1e-3) / 1e6, "ms_per_step": ms, "steps": steps,
+                     "hbm_frac": bytes_ * w.N / (ms * 1e-3) / 1e9 / hbm_peak}
+        g.close()
+    del fields
+    cmp = {}
+    for name, model, alpha in (("basic", rlb.MODEL_BASIC, 0.0), ("extended", rlb.MODEL_EXTENDED, 0.15)):
+        t = W.riemann_tube(800, 32.0, 2.0, eta_over_s=0.01, dt_over_dx=0.25, alpha_override=alpha)
+        g = rlb.Grid(t.nx, eta_over_s=0.01, dt_over_dx=0.25, alpha_override=alpha, precision=rlb.FP64,
+                     model=model)
+        g.init(*t.fields())
+        done, status = 0, "physical after 1200 steps"
+        while done < 1200:
+            try:
+                g.step(50)
+            except rlb.RLBError as e:
+                status = f"{rlb.status_string(e.status)} within steps {done + 1}-{done + 50}"
+                break
+            done += 50
+        cmp[name] = status
+        g.close()
+    out["paper_comparison_beta07"] = {"setup": "800-cell tube, P ratio 32, eta/s 0.01, dt/dx 0.25, FP64; "
+                                               "alpha 0 (basic), 0.15 (extended)", **cmp}
+    return out
+
+
 def run_ours(args):
     global _dist
     import torch
@@ -448,6 +500,7 @@ def run_ours(args):
 
     batch = batch_sweep(torch, rlb, W, hbm_peak, local) if not args.no_batch else None
     sphere = sphere_run(torch, rlb, W, local) if not args.no_batch else None
+    basic = basic_model_run(torch, rlb, W, hbm_peak) if not args.no_batch else None
     if rank != 0:
         return 0
     l1 = l1_fp32_vs_fp64(torch)
@@ -478,6 +531,7 @@ def run_ours(args):
         "cpu_baseline": base,
         "batch": batch,
         "sphere_cloud": sphere,
+        "basic_model": basic,
     }
     print(json.dumps(line), flush=True)
     if _dist is not None:
@@ -492,7 +546,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batch", action="store_true",
-                    help="skip the 512-tube batched sweep and the sphere-cloud run")
+                    help="skip the batched sweep, the sphere-cloud run and the basic-model runs")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
