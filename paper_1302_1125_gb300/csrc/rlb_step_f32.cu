@@ -1,6 +1,8 @@
 // FP32-storage form of the fused step (see rlb_step_f32.cuh): populations
 // stored, streamed and relaxed in float, two cells per thread, double-float
 // moment sums, no FP64 instructions.
+#include <atomic>
+
 #include "rlb_step_f32.cuh"
 
 namespace rlb {
@@ -21,12 +23,19 @@ static cudaError_t launch_f32(const StepParams &p, const float *f, const float *
         grid = dim3((npairs + 31) / 32, (p.ny + RLB_F32_BY - 1) / RLB_F32_BY, p.nz);
     }
     const size_t smem = f32::step_smem_bytes(int(block.x * block.y), f32::kStageOn && VEC2 && !EULER, DIM);
-    static bool attr_set = false;   // per instantiation
-    if (!attr_set) {
-        const cudaError_t e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2, LAT>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    // the shared-memory limit is a per-device attribute of the kernel: set it
+    // once per device and instantiation (a repeated set is harmless, so the
+    // flags need no lock)
+    constexpr int kMaxDevices = 64;
+    static std::atomic<bool> attr_set[kMaxDevices];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= kMaxDevices || !attr_set[dev].load(std::memory_order_acquire)) {
+        e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2, LAT>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        if (dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
     }
     f32::step_f32_kernel<DIM, EULER, VEC2, LAT><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev);
     return cudaGetLastError();
