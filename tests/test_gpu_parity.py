@@ -159,6 +159,42 @@ def test_fp32_form_l1_error_against_fp64_oracle(orc):
     print("FP32 L1 errors (n, e, u_x):", report)
 
 
+def _euler(w):
+    w.euler_mode = 1
+    return w
+
+
+def _all_outflow(w):
+    w.bc_lo = w.bc_hi = (1, 1, 1)
+    w.eta_over_s = 0.05
+    return w
+
+
+# the FP32-storage kernel's other paths: staging with wrap-around in x, y and
+# z (even nx), the unstaged path (odd nx), Euler mode (unstaged), open faces
+FP32_CASES = {
+    "even_3d_periodic_box": (lambda: _box(36, 14, 10, 12, tau_override=0.0, alpha_override=0.1), 80),
+    "ragged_3d_box": (lambda: _box(37, 13, 11, 1, tau_override=0.0, alpha_override=0.1), 60),
+    "outflow_every_face": (lambda: _all_outflow(_box(20, 12, 10, 8, tau_override=0.0, alpha_override=0.1)), 40),
+    "euler_tube": (lambda: _euler(W.riemann_tube(400, 1000.0, 1000.0 ** 0.25, dt_over_dx=0.15,
+                                                 alpha_override=0.2)), 300),
+    "euler_3d_box": (lambda: _euler(_box(18, 10, 8, 9, tau_override=0.0, alpha_override=0.1)), 80),
+    "tiny_2x1x1": (lambda: _box(2, 1, 1, 4), 20),
+}
+
+
+@pytest.mark.parametrize("name", sorted(FP32_CASES))
+def test_fp32_paths_l1_error_against_fp64_oracle(orc, name):
+    make, steps = FP32_CASES[name]
+    w = make()
+    _, mg = run_gpu(w, steps, rlb.FP32_STORAGE)
+    _, mo = run_oracle(orc, w, steps)
+    errs = [l1rel(mg[k], mo[k]) for k in (0, 1)]
+    # velocity components against the scale of gamma u (zero-mean fields)
+    errs += [float(np.sum(np.abs(mg[k] - mo[k])) / np.sum(np.abs(mo[5]))) for k in (2, 3, 4)]
+    assert max(errs) <= FP32_L1_TOL, (name, errs)
+
+
 @pytest.mark.parametrize("precision,tol", [(rlb.FP64, 1e-13), (rlb.FP32_STORAGE, 1e-6)])
 def test_conservation_drift(precision, tol):
     w = _box(48, 40, 1, 11, tau_override=0.8, alpha_override=0.15)
