@@ -176,11 +176,19 @@ def barrier():
 
 
 def max_over_ranks(torch, v: float) -> float:
+    """the largest v over the ranks (the job's time is its slowest replica's)"""
     if _dist is None:
         return v
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cuda" if _dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     _dist.all_reduce(t, op=_dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world: int, units_per_rank: float, seconds: float) -> float:
+    """whole-job throughput in millions of units per second: every replica
+    processes units_per_rank in the (max-over-ranks) time"""
+    return world * units_per_rank / seconds / 1e6
 
 
 def cpu_baseline(steps=None, warmup=1, budget_s=12.0):
@@ -463,7 +471,7 @@ def run_ours(args):
     ms, clk, launches = timed_steps(torch, g, args.steps, args.warmup, local)
     ms = max_over_ranks(torch, ms)
     per_step = ms / args.steps
-    value = world * N * args.steps / (ms * 1e-3) / 1e6
+    value = job_value(world, N * args.steps, ms * 1e-3)
     achieved = BYTES_FP32 * N / (per_step * 1e-3) / 1e9
     g.close()
 
