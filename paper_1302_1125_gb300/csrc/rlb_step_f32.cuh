@@ -195,6 +195,28 @@ __device__ __forceinline__ int off_of(const Geo &g, const StepParams &p, int d)
     else return g.zoff[k];
 }
 
+// Divisions and the logarithm of the per-cell scalar work (recovery, tau,
+// kappa, 1/gamma): the fast intrinsics (a few ulp, operands far from the
+// range limits of __fdividef) unless RLB_F32_IEEE_DIV is defined.  The
+// conserved sums do not depend on them: the equilibrium's lattice sums are
+// set to exact targets afterwards (weigh2).
+__device__ __forceinline__ float fdiv(float a, float b)
+{
+#ifdef RLB_F32_IEEE_DIV
+    return a / b;
+#else
+    return __fdividef(a, b);
+#endif
+}
+__device__ __forceinline__ float flog(float a)
+{
+#ifdef RLB_F32_IEEE_DIV
+    return logf(a);
+#else
+    return __logf(a);
+#endif
+}
+
 struct Mac2 {
     f2 P, ux, uy, uz, n;
 };
@@ -225,7 +247,7 @@ __device__ __forceinline__ void coef_h2(const Mac2 &m, f2 &K0, f2 (&Kb)[3], f2 (
 {
     const f2 u2p = fma2(m.ux, m.ux, fma2(m.uy, m.uy, m.uz * m.uz));
     const f2 g = f2{sqrtf(1.0f + u2p.x), sqrtf(1.0f + u2p.y)};
-    const f2 ig = f2{1.0f / g.x, 1.0f / g.y};
+    const f2 ig = f2{fdiv(1.0f, g.x), fdiv(1.0f, g.y)};
     const f2 ux = m.ux * ig, uy = m.uy * ig, uz = m.uz * ig;
     const f2 B = m.n * g;
     const f2 uu = fma2(ux, ux, fma2(uy, uy, uz * uz));
@@ -331,15 +353,15 @@ __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 
     const f2 root2 = fma2(E, E, bc(3.0f) * D);
     const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
     Mac2 m;
-    m.P = f2{D.x / den.x, D.y / den.y};
+    m.P = f2{fdiv(D.x, den.x), fdiv(D.y, den.y)};
     const f2 fourP = bc(4.0f) * m.P;
-    const f2 g2 = f2{(E.x + m.P.x) / fourP.x, (E.y + m.P.y) / fourP.y};
+    const f2 g2 = f2{fdiv(E.x + m.P.x, fourP.x), fdiv(E.y + m.P.y, fourP.y)};
     const f2 g = f2{sqrtf(g2.x), sqrtf(g2.y)};
-    const f2 s = f2{kXi0 / (fourP.x * g.x), kXi0 / (fourP.y * g.y)};
+    const f2 s = f2{fdiv(kXi0, fourP.x * g.x), fdiv(kXi0, fourP.y * g.y)};
     m.ux = (Vx.hi + Vx.lo) * s;
     m.uy = (Vy.hi + Vy.lo) * s;
     m.uz = (Vz.hi + Vz.lo) * s;
-    m.n = f2{kXi0 * Sh.x / g.x, kXi0 * Sh.y / g.y};
+    m.n = f2{fdiv(kXi0 * Sh.x, g.x), fdiv(kXi0 * Sh.y, g.y)};
     ok0 = E.x > 0.0f && D.x > 0.0f && isfinite(m.n.x) && isfinite(s.x);
     ok1 = E.y > 0.0f && D.y > 0.0f && isfinite(m.n.y) && isfinite(s.y);
     return m;
@@ -357,14 +379,14 @@ __device__ __forceinline__ Mac2 recover2f(f2 S, f2 Vx, f2 Vy, f2 Vz, f2 Sh)
     const f2 root2 = fma2(E, E, bc(3.0f) * D);
     const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
     Mac2 m;
-    m.P = f2{D.x / den.x, D.y / den.y};
+    m.P = f2{fdiv(D.x, den.x), fdiv(D.y, den.y)};
     const f2 fourP = bc(4.0f) * m.P;
-    const f2 g = f2{sqrtf((E.x + m.P.x) / fourP.x), sqrtf((E.y + m.P.y) / fourP.y)};
-    const f2 s = f2{kXi0 / (fourP.x * g.x), kXi0 / (fourP.y * g.y)};
+    const f2 g = f2{sqrtf(fdiv(E.x + m.P.x, fourP.x)), sqrtf(fdiv(E.y + m.P.y, fourP.y))};
+    const f2 s = f2{fdiv(kXi0, fourP.x * g.x), fdiv(kXi0, fourP.y * g.y)};
     m.ux = Vx * s;
     m.uy = Vy * s;
     m.uz = Vz * s;
-    m.n = f2{kXi0 * Sh.x / g.x, kXi0 * Sh.y / g.y};
+    m.n = f2{fdiv(kXi0 * Sh.x, g.x), fdiv(kXi0 * Sh.y, g.y)};
     return m;
 }
 
@@ -372,10 +394,10 @@ __device__ __forceinline__ Mac2 recover2f(f2 S, f2 Vx, f2 Vy, f2 Vz, f2 Sh)
 template <int LAT>
 __device__ __forceinline__ float tau1(float P, float n, float eta_over_s)
 {
-    const float T = P / n;
-    const float lam = n * float(kPi2Over16) / (T * T * T);
-    const float sfac = fmaxf(4.0f - logf(lam), float(kSMin));
-    return 0.5f + Lat<LAT>::f_nu2 * eta_over_s * sfac / (4.0f * T);
+    const float T = fdiv(P, n);
+    const float lam = fdiv(n * float(kPi2Over16), T * T * T);
+    const float sfac = fmaxf(4.0f - flog(lam), float(kSMin));
+    return 0.5f + fdiv(Lat<LAT>::f_nu2 * eta_over_s * sfac, 4.0f * T);
 }
 
 // streaming increment of population I along axis A for the pair (+ bulk lap)
@@ -611,8 +633,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                 t1 = tau1<LAT>(mt.P.y, mt.n.y, eos);
             }
             const float kw = p.f_kw;
-            const float w0 = kw / t0, w1 = kw / t1;
-            kap = f2{w0 / (1.0f + w0), w1 / (1.0f + w1)};
+            const float w0 = fdiv(kw, t0), w1 = fdiv(kw, t1);
+            kap = f2{fdiv(w0, 1.0f + w0), fdiv(w1, 1.0f + w1)};
         }
 
         // the previous level holds the raw moment sums of time t - dt, so the
