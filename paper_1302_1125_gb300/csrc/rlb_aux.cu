@@ -2,6 +2,7 @@
 #include <utility>
 
 #include "rlb_cellops.cuh"
+#include "rlb_cellops_f32.cuh"
 
 namespace rlb {
 
@@ -37,6 +38,46 @@ __global__ void solid_reset_kernel(int M, const int *__restrict__ idx, long long
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= M) return;
     init_cell<T, LAT>(0, idx[j], ps, st, st + 1, st + 2, st + 2, st + 2, f, h, prev, status);
+}
+
+// FP32-storage forms of the three kernels above, two cells per thread in
+// float arithmetic (rlb_cellops_f32.cuh): consecutive cells i0 = 2 t, i0 + 1
+template <int LAT>
+__global__ void init_kernel_f32(int N, long long ps, const double *__restrict__ n, const double *__restrict__ Tt,
+                                const double *__restrict__ ux, const double *__restrict__ uy,
+                                const double *__restrict__ uz, float *__restrict__ f, float *__restrict__ h,
+                                float *__restrict__ prev, unsigned *status)
+{
+    const long long i0 = 2LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= N) return;
+    const bool has1 = i0 + 1 < N;
+    const long long i1 = has1 ? i0 + 1 : i0;
+    f32::init_pair<LAT, true>(f32::CellPair{i0, i1, i0, i1, has1}, ps, n, Tt, ux, uy, uz, f, h, prev, status);
+}
+
+template <int LAT>
+__global__ void macro_kernel_f32(int N, long long ps, const float *__restrict__ f, const float *__restrict__ h,
+                                 double *__restrict__ out, unsigned *status)
+{
+    const long long i0 = 2LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+    if (i0 >= N) return;
+    const bool has1 = i0 + 1 < N;
+    const long long i1 = has1 ? i0 + 1 : i0;
+    f32::macro_pair<LAT, true>(f32::CellPair{i0, i1, i0, i1, has1}, ps, f, h, out, N, status);
+}
+
+// solid cells idx[2 t] and idx[2 t + 1], both from the state st = {n, T, 0}
+template <int LAT>
+__global__ void solid_reset_kernel_f32(int M, const int *__restrict__ idx, long long ps,
+                                       const double *__restrict__ st, float *__restrict__ f, float *__restrict__ h,
+                                       float *__restrict__ prev, unsigned *status)
+{
+    const int j = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (j >= M) return;
+    const bool has1 = j + 1 < M;
+    const long long d0 = idx[j], d1 = has1 ? idx[j + 1] : d0;
+    f32::init_pair<LAT, false>(f32::CellPair{0, 0, d0, d1, has1}, ps, st, st + 1, st + 2, st + 2, st + 2, f, h,
+                               prev, status);
 }
 
 // per-block partial sums of (T^00, T^0x, T^0y, T^0z, N^0); fixed grid and
@@ -91,12 +132,12 @@ cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const do
                         const double *ux, const double *uy, const double *uz, void *f, void *h,
                         void *prev, unsigned *status, cudaStream_t s, int lat)
 {
-    const int b = 128, g = (N + b - 1) / b;
+    const int b = 128, g = (N + b - 1) / b, g2 = (N + 2 * b - 1) / (2 * b);
     auto go = [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         if (fp32)
-            init_kernel<float, L><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (float *)f, (float *)h,
-                                                  (float *)prev, status);
+            init_kernel_f32<L><<<g2, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (float *)f, (float *)h, (float *)prev,
+                                                status);
         else
             init_kernel<double, L><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (double *)f, (double *)h,
                                                    (double *)prev, status);
@@ -109,11 +150,11 @@ cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const do
 cudaError_t launch_macro(int fp32, int N, long long ps, const void *f, const void *h, double *out,
                          unsigned *status, cudaStream_t s, int lat)
 {
-    const int b = 128, g = (N + b - 1) / b;
+    const int b = 128, g = (N + b - 1) / b, g2 = (N + 2 * b - 1) / (2 * b);
     auto go = [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         if (fp32)
-            macro_kernel<float, L><<<g, b, 0, s>>>(N, ps, (const float *)f, (const float *)h, out, status);
+            macro_kernel_f32<L><<<g2, b, 0, s>>>(N, ps, (const float *)f, (const float *)h, out, status);
         else
             macro_kernel<double, L><<<g, b, 0, s>>>(N, ps, (const double *)f, (const double *)h, out,
                                                     status);
@@ -126,12 +167,12 @@ cudaError_t launch_macro(int fp32, int N, long long ps, const void *f, const voi
 cudaError_t launch_solid_reset(int fp32, int M, const int *idx, long long ps, const double *st, void *f,
                                void *h, void *prev, unsigned *status, cudaStream_t s, int lat)
 {
-    const int b = 128, g = (M + b - 1) / b;
+    const int b = 128, g = (M + b - 1) / b, g2 = (M + 2 * b - 1) / (2 * b);
     auto go = [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         if (fp32)
-            solid_reset_kernel<float, L><<<g, b, 0, s>>>(M, idx, ps, st, (float *)f, (float *)h, (float *)prev,
-                                                         status);
+            solid_reset_kernel_f32<L><<<g2, b, 0, s>>>(M, idx, ps, st, (float *)f, (float *)h, (float *)prev,
+                                                       status);
         else
             solid_reset_kernel<double, L><<<g, b, 0, s>>>(M, idx, ps, st, (double *)f, (double *)h,
                                                           (double *)prev, status);

@@ -1,7 +1,8 @@
 // Batched tubes: initialisation, macroscopic output and per-tube totals over
 // the tube storage (packed fields in, packed fields out), and the dispatch of
 // the persistent step kernel.
-#include "rlb_cellops.cuh"
+#include "rlb_cellops_f32.cuh"
+#include "rlb_kernels.cuh"
 #include "rlb_internal.h"
 
 namespace rlb {
@@ -15,17 +16,20 @@ cudaError_t launch_tubes(const Args &a, int threads, int bound, int cluster, cud
     return launch_tubes_cg(a, threads, bound, cluster, s, nclusters_out);
 }
 
-// grid (ceil(max_nx / 128), B): cell x of tube blockIdx.y
+// grid (ceil(max_nx / 256), B): cells x0 = 2 t and x0 + 1 of tube blockIdx.y
 __global__ void tubes_init_kernel(const Tube *__restrict__ tubes, const long long *__restrict__ pack, long long ps,
                                   const double *__restrict__ n, const double *__restrict__ T,
                                   const double *__restrict__ ux, float *__restrict__ f, float *__restrict__ h,
                                   float *__restrict__ prev, unsigned *status)
 {
     const int b = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const Tube t = tubes[b];
-    if (x >= t.nx) return;
-    init_cell<float>(pack[b] + x, (long long)t.off + x, ps, n, T, ux, nullptr, nullptr, f, h, prev, status);
+    if (x0 >= t.nx) return;
+    const bool has1 = x0 + 1 < t.nx;
+    const long long s0 = pack[b] + x0, d0 = (long long)t.off + x0;
+    const f32::CellPair c{s0, has1 ? s0 + 1 : s0, d0, has1 ? d0 + 1 : d0, has1};
+    f32::init_pair<0, false>(c, ps, n, T, ux, nullptr, nullptr, f, h, prev, status);
 }
 
 __global__ void tubes_macro_kernel(const Tube *__restrict__ tubes, const long long *__restrict__ pack,
@@ -35,11 +39,14 @@ __global__ void tubes_macro_kernel(const Tube *__restrict__ tubes, const long lo
                                    double *__restrict__ out, unsigned *status)
 {
     const int b = blockIdx.y;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const Tube t = tubes[b];
-    if (x >= t.nx) return;
+    if (x0 >= t.nx) return;
+    const bool has1 = x0 + 1 < t.nx;
     const bool one = par[b] != 0;
-    macro_cell<float>((long long)t.off + x, ps, one ? f1 : f0, one ? h1 : h0, out, pack[b] + x, total, status);
+    const long long s0 = (long long)t.off + x0, d0 = pack[b] + x0;
+    const f32::CellPair c{s0, has1 ? s0 + 1 : s0, d0, has1 ? d0 + 1 : d0, has1};
+    f32::macro_pair<0, false>(c, ps, one ? f1 : f0, one ? h1 : h0, out, total, status);
 }
 
 // class of population i under the 1-D symmetry reduction, as the plane of
@@ -121,7 +128,7 @@ cudaError_t launch_tubes_init(int B, int max_nx, const Tube *tubes, const long l
                               const double *n, const double *T, const double *ux, float *f, float *h,
                               float *prev, unsigned *status, cudaStream_t s)
 {
-    const dim3 grid((max_nx + 127) / 128, B, 1);
+    const dim3 grid((max_nx + 255) / 256, B, 1);
     tubes_init_kernel<<<grid, 128, 0, s>>>(tubes, pack, ps, n, T, ux, f, h, prev, status);
     return cudaGetLastError();
 }
@@ -131,7 +138,7 @@ cudaError_t launch_tubes_macro(int B, int max_nx, const Tube *tubes, const long 
                                const float *f1, const float *h1, double *out, unsigned *status,
                                cudaStream_t s)
 {
-    const dim3 grid((max_nx + 127) / 128, B, 1);
+    const dim3 grid((max_nx + 255) / 256, B, 1);
     tubes_macro_kernel<<<grid, 128, 0, s>>>(tubes, pack, par, ps, total, f0, h0, f1, h1, out, status);
     return cudaGetLastError();
 }

@@ -1,5 +1,6 @@
-// rlb_cellops.cuh -- per-cell initialisation and macroscopic output, shared by the
-// grid kernels (rlb_aux.cu) and the batched tube kernels (rlb_batch.cu).
+// rlb_cellops.cuh -- per-cell initialisation and macroscopic output of the FP64
+// form (the FP32-storage form has its own, in float arithmetic:
+// rlb_cellops_f32.cuh).
 #pragma once
 
 #include "rlb_kernels.cuh"
@@ -31,32 +32,16 @@ __device__ __forceinline__ void init_cell(long long in, long long idx, long long
     const EqW<T> kf = weigh_f<T, LAT>(a);
     coef_h<LAT>(m, a);
     const EqW<T> kh = weigh_h<T, LAT>(a);
-    double S = 0.0, Vx = 0.0, Vy = 0.0, Vz = 0.0, Sh = 0.0;
     for_pops(RLB_POPS, [&](auto ic) {
         constexpr int I = decltype(ic)::value;
-        const T fv = eq_pop<I>(kf), hv = eq_pop<I>(kh);
-        f[I * ps + idx] = fv;
-        h[I * ps + idx] = hv;
-        S += double(fv);
-        Sh += double(hv);
-        if constexpr (cdir<I, 0, LAT>() != 0) Vx += double(cdir<I, 0, LAT>()) * double(fv);
-        if constexpr (cdir<I, 1, LAT>() != 0) Vy += double(cdir<I, 1, LAT>()) * double(fv);
-        if constexpr (cdir<I, 2, LAT>() != 0) Vz += double(cdir<I, 2, LAT>()) * double(fv);
+        f[I * ps + idx] = eq_pop<I>(kf);
+        h[I * ps + idx] = eq_pop<I>(kh);
     });
-    if constexpr (sizeof(T) == 4) {
-        // FP32-storage form: the previous level is the raw moment sums
-        prev[0 * ps + idx] = T(S);
-        prev[1 * ps + idx] = T(Vx);
-        prev[2 * ps + idx] = T(Vy);
-        prev[3 * ps + idx] = T(Vz);
-        prev[4 * ps + idx] = T(Sh);
-    } else {
-        prev[0 * ps + idx] = T(m.P);
-        prev[1 * ps + idx] = T(m.ux);
-        prev[2 * ps + idx] = T(m.uy);
-        prev[3 * ps + idx] = T(m.uz);
-        prev[4 * ps + idx] = T(m.n);
-    }
+    prev[0 * ps + idx] = T(m.P);
+    prev[1 * ps + idx] = T(m.ux);
+    prev[2 * ps + idx] = T(m.uy);
+    prev[3 * ps + idx] = T(m.uz);
+    prev[4 * ps + idx] = T(m.n);
 }
 
 // moments + recovery of the populations at plane index `idx`: n, e, u_x,

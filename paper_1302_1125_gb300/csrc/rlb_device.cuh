@@ -232,6 +232,21 @@ __device__ __forceinline__ R minmod(R a, R b)
     return (a > R(0) && b > R(0)) ? m : ((a < R(0) && b < R(0)) ? -m : R(0));
 }
 
+// Eq. 53 for doubles on the bit patterns, so that the limiter issues integer
+// instructions instead of occupying the FP64 pipe (GB300: 2 per clock per
+// SM): the magnitudes of non-negative doubles order as unsigned integers,
+// the signs agree when the top bits do.  The value equals the floating-point
+// form's (a zero may carry the sign of a).
+template <>
+__device__ __forceinline__ double minmod<double>(double a, double b)
+{
+    const unsigned long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    constexpr unsigned long long kSign = 0x8000000000000000ULL;
+    const unsigned long long ma = ia & ~kSign, mb = ib & ~kSign;
+    const unsigned long long m = ma < mb ? ma : mb;
+    return __longlong_as_double(((ia ^ ib) & kSign) ? 0ULL : (m | (ia & kSign)));
+}
+
 // Neighbour map of one axis: linear offsets of the cells at d = -2, -1, +1, +2
 // after the boundary rule, and a mask of inlet ghost cells.
 struct AxisNbr {

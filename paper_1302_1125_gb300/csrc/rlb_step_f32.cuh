@@ -341,11 +341,16 @@ __device__ __forceinline__ f2 eq2(const W2 &e)
 // E^2 - |M|^2 = xi0^2 (xi0^2 S^2 - |V|^2) formed in double-float,
 // P = (E^2 - |M|^2) / (E + sqrt(E^2 + 3 (E^2 - |M|^2))), gamma^2 = (E + P)/(4 P),
 // u' = M / (4 P gamma), n = N^0 / gamma
-template <int LAT>
+// (FAST = false: IEEE division, for the macroscopic output)
+template <int LAT, bool FAST = true>
 __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 &Vy, const df2 &Vz,
                                          f2 Sh, bool &ok0, bool &ok1)
 {
     constexpr float kXi0 = float(Lat<LAT>::xi0), kXi0Sq = float(Lat<LAT>::xi0sq);
+    auto dv = [](float a, float b) {
+        if constexpr (FAST) return fdiv(a, b);
+        else return a / b;
+    };
     const df2 V2 = dadd(dadd(sq(Vx), sq(Vy)), sq(Vz));
     const df2 Dr = dadd(dscale(sq(S), Xi0Sq<LAT>::hi, Xi0Sq<LAT>::lo), dneg(V2));
     const f2 D = bc(kXi0Sq) * (Dr.hi + Dr.lo);
@@ -353,15 +358,15 @@ __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 
     const f2 root2 = fma2(E, E, bc(3.0f) * D);
     const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
     Mac2 m;
-    m.P = f2{fdiv(D.x, den.x), fdiv(D.y, den.y)};
+    m.P = f2{dv(D.x, den.x), dv(D.y, den.y)};
     const f2 fourP = bc(4.0f) * m.P;
-    const f2 g2 = f2{fdiv(E.x + m.P.x, fourP.x), fdiv(E.y + m.P.y, fourP.y)};
+    const f2 g2 = f2{dv(E.x + m.P.x, fourP.x), dv(E.y + m.P.y, fourP.y)};
     const f2 g = f2{sqrtf(g2.x), sqrtf(g2.y)};
-    const f2 s = f2{fdiv(kXi0, fourP.x * g.x), fdiv(kXi0, fourP.y * g.y)};
+    const f2 s = f2{dv(kXi0, fourP.x * g.x), dv(kXi0, fourP.y * g.y)};
     m.ux = (Vx.hi + Vx.lo) * s;
     m.uy = (Vy.hi + Vy.lo) * s;
     m.uz = (Vz.hi + Vz.lo) * s;
-    m.n = f2{fdiv(kXi0 * Sh.x, g.x), fdiv(kXi0 * Sh.y, g.y)};
+    m.n = f2{dv(kXi0 * Sh.x, g.x), dv(kXi0 * Sh.y, g.y)};
     ok0 = E.x > 0.0f && D.x > 0.0f && isfinite(m.n.x) && isfinite(s.x);
     ok1 = E.y > 0.0f && D.y > 0.0f && isfinite(m.n.y) && isfinite(s.y);
     return m;
