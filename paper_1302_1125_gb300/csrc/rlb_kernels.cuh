@@ -36,49 +36,59 @@ __device__ __forceinline__ T nbr(const T *q, int idx, const AxisNbr &a, int k, T
     return ((a.ghost >> k) & 1u) ? ghost : ldg(q + idx + a.off[k]);
 }
 
-// Streaming increment of one population along axis A: minus dt (c0/ct) times
-// the conservative minmod flux difference h^a(x) - h^a(x - e_a) (Eqs. 47-53),
-// and, for f with i != 0, the central second difference for the bulk term.
-template <typename T, bool IS_F, int I, int A, int LAT>
+// Streaming terms of one population along axis A (Eqs. 47-53): the
+// accumulator acc receives minus dt (c0/ct) times the conservative minmod
+// flux difference h^a(x) - h^a(x - e_a); for f with i != 0 the neighbour sum
+// s receives q(x + e_A) + q(x - e_A) of the bulk term's second difference
+// (assigned on the first axis, FIRST).
+template <typename T, bool IS_F, int I, int A, int LAT, bool FIRST>
 __device__ __forceinline__ void axis_terms(const T *q, int idx, const AxisNbr &an, T qc, T ghost,
-                                           T k1, T k2, T hl, T &inc, T &lap)
+                                           T k1, T k2, T hl, T &acc, T &s)
 {
     constexpr int c = cdir<I, A, LAT>();
     constexpr bool need_lap = IS_F && I != 0;
+    auto add_s = [&](T qm1, T qp1) {
+        if constexpr (need_lap) {
+            if constexpr (FIRST) s = qp1 + qm1;
+            else s += qp1 + qm1;
+        }
+    };
     if constexpr (c > 0) {
         const T qm2 = nbr(q, idx, an, 0, ghost);
         const T qm1 = nbr(q, idx, an, 1, ghost);
         const T qp1 = nbr(q, idx, an, 2, ghost);
         const T d0 = qm1 - qm2, d1 = qc - qm1, d2 = qp1 - qc;
         const T D = d1 + hl * (minmod(d2, d1) - minmod(d1, d0));
-        inc -= (c == 1 ? k1 : k2) * D;
-        if constexpr (need_lap) lap += (qp1 - qc) - d1;
+        acc -= (c == 1 ? k1 : k2) * D;
+        add_s(qm1, qp1);
     } else if constexpr (c < 0) {
         const T qm1 = nbr(q, idx, an, 1, ghost);
         const T qp1 = nbr(q, idx, an, 2, ghost);
         const T qp2 = nbr(q, idx, an, 3, ghost);
         const T e0 = qc - qm1, e1 = qp1 - qc, e2 = qp2 - qp1;
         const T D = e1 - hl * (minmod(e1, e2) - minmod(e0, e1));
-        inc += (c == -1 ? k1 : k2) * D;
-        if constexpr (need_lap) lap += e1 - e0;
+        acc += (c == -1 ? k1 : k2) * D;
+        add_s(qm1, qp1);
     } else if constexpr (need_lap) {
-        const T qm1 = nbr(q, idx, an, 1, ghost);
-        const T qp1 = nbr(q, idx, an, 2, ghost);
-        lap += (qp1 - qc) - (qc - qm1);
+        add_s(nbr(q, idx, an, 1, ghost), nbr(q, idx, an, 2, ghost));
     }
 }
 
-// f + streaming (+ bulk) for population I: the explicit part of Eq. 57
+// f + streaming (+ bulk) for population I: the explicit part of Eq. 57.  The
+// bulk term's central second difference sum_A [q(x + e_A) - 2 q(x) + q(x - e_A)]
+// is taken as s - 2 DIM q(x) in one fused operation (exact coefficients, so
+// that its sum over a periodic grid carries no systematic rounding).
 template <typename T, int DIM, bool IS_F, int I, int LAT>
 __device__ __forceinline__ T streamed(const T *q, int idx, const AxisNbr (&am)[3], T qc, T ghost,
                                       T k1, T k2, T hl, T kbulk)
 {
-    T inc = T(0), lap = T(0);
-    axis_terms<T, IS_F, I, 0, LAT>(q, idx, am[0], qc, ghost, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 1) axis_terms<T, IS_F, I, 1, LAT>(q, idx, am[1], qc, ghost, k1, k2, hl, inc, lap);
-    if constexpr (DIM > 2) axis_terms<T, IS_F, I, 2, LAT>(q, idx, am[2], qc, ghost, k1, k2, hl, inc, lap);
-    if constexpr (IS_F && I != 0) inc += kbulk * lap;
-    return qc + inc;
+    constexpr bool need_lap = IS_F && I != 0;
+    T acc = qc, s = T(0);
+    axis_terms<T, IS_F, I, 0, LAT, true>(q, idx, am[0], qc, ghost, k1, k2, hl, acc, s);
+    if constexpr (DIM > 1) axis_terms<T, IS_F, I, 1, LAT, false>(q, idx, am[1], qc, ghost, k1, k2, hl, acc, s);
+    if constexpr (DIM > 2) axis_terms<T, IS_F, I, 2, LAT, false>(q, idx, am[2], qc, ghost, k1, k2, hl, acc, s);
+    if constexpr (need_lap) acc += kbulk * fma(T(-2 * DIM), qc, s);
+    return acc;
 }
 
 template <typename T>
