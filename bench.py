@@ -2,7 +2,8 @@
 """Throughput of the fused RLB time step on GB300.
 
 Workload: the 3-D shock-cloud, 512 x 256 x 256 cells (33.5 M), FP32
-population storage with FP64 moments and recovery; a step is one time step
+population storage and arithmetic (moment sums in double-float, i.e. float
+pairs; no FP64 instruction); a step is one time step
 of the whole grid (every cell: minmod streaming of 38 populations, bulk
 Laplacian, moments, Landau recovery, equilibria, implicit update).  The FP64
 form is timed on the same grid for the FP32/FP64 ratio, and the FP32 form's
@@ -516,12 +517,12 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 storage (f64 moments/recovery)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": "cloud_3d: 3-D shock-cloud 512x256x256 (slab-driven shock, pressure "
                                "ratio 10; cloud r=48 at (180,128,128), density x10, pressure balanced); "
                                "eta/s 0.05, alpha 0.2, dt/dx 0.15",
-                   "cells": N, "precision": "FP32 populations, FP64 moments and recovery",
+                   "cells": N, "precision": "FP32 populations and arithmetic, double-float moment sums",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: 10.2 GB of populations read+written per step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
