@@ -127,6 +127,8 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.symmetry_1d != 0)
         return fail(ctx, RLB_E_INVALID, "the 1-D symmetry reduction is available for batched tubes (rlb_batch_create)");
     if (o.model != 0 && o.model != 1) return fail(ctx, RLB_E_INVALID, "model must be 0 (extended) or 1 (basic)");
+    if (o.thread_mapping < 0 || o.thread_mapping > 2)
+        return fail(ctx, RLB_E_INVALID, "thread_mapping must be 0 (automatic), 1 (tiles) or 2 (linear)");
     if (!std::isfinite(o.tau_override) || !std::isfinite(o.alpha_override))
         return fail(ctx, RLB_E_INVALID, "overrides must be finite");
     // explicit stability bounds
@@ -198,6 +200,7 @@ void rlb_default_options(rlb_options *o)
     o->cuda_stream = nullptr;
     o->symmetry_1d = 0;
     o->model = 0;
+    o->thread_mapping = 0;
 }
 
 rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
@@ -292,6 +295,7 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
     }
     sp.half_lim = limiter == RLB_LIMITER_MINMOD ? 0.5 : 0.0;
     sp.lat = o.model;
+    sp.mapping = o.thread_mapping;
     sp.k1 = lat_c0ct(o.model) * o.dt_over_dx;
     sp.k2 = double(lat_dmag(o.model)) * lat_c0ct(o.model) * o.dt_over_dx;
     sp.kw = lat_omegaC(o.model) * o.dt_over_dx;

@@ -17,10 +17,22 @@ static cudaError_t launch_f32(const StepParams &p, const float *f, const float *
         block = dim3(128, 1, 1);
         grid = dim3((npairs + 127) / 128, 1, 1);
     } else {
-        // 32 x 8 threads (64 x 8 cells), two blocks per SM at <= 128 registers:
-        // the best of a sweep over block shapes and register caps on GB300
-        block = dim3(32, RLB_F32_BY, 1);
-        grid = dim3((npairs + 31) / 32, (p.ny + RLB_F32_BY - 1) / RLB_F32_BY, p.nz);
+        // tiles of 32 x 8 threads (64 x 8 cells), two blocks per SM at <= 128
+        // registers: the best of a sweep over block shapes and register caps on
+        // GB300 when nx fills them; otherwise the same 256 threads take 256
+        // consecutive pairs of the x-fastest order (the kernel reads the
+        // mapping from the block shape)
+        const long long tiles_x = (npairs + 31) / 32, tiles_y = (p.ny + RLB_F32_BY - 1) / RLB_F32_BY;
+        const long long pairs = (long long)npairs * p.ny * p.nz;
+        const double fill = double(npairs) * p.ny / double(tiles_x * 32 * tiles_y * RLB_F32_BY);
+        const bool linear = p.mapping == 2 || (p.mapping == 0 && fill < 0.97);
+        if (linear) {
+            block = dim3(32 * RLB_F32_BY, 1, 1);
+            grid = dim3(unsigned((pairs + 32 * RLB_F32_BY - 1) / (32 * RLB_F32_BY)), 1, 1);
+        } else {
+            block = dim3(32, RLB_F32_BY, 1);
+            grid = dim3(unsigned(tiles_x), unsigned(tiles_y), p.nz);
+        }
     }
     const size_t smem = f32::step_smem_bytes(int(block.x * block.y), f32::kStageOn && VEC2 && !EULER, DIM);
     // the shared-memory limit is a per-device attribute of the kernel: set it

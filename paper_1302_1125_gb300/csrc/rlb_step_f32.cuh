@@ -793,10 +793,25 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
                     float *__restrict__ fo, float *__restrict__ ho, float *__restrict__ prev)
 {
     extern __shared__ f2 s_park[];
-    const int x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x0 >= p.nx || y >= p.ny) return;
+    // the block shape gives the mapping: blocks of one row take consecutive
+    // pairs t of the x-fastest order (rows of ceil(nx / 2) pairs; the 1-D
+    // form, and grids whose nx does not fill the tiles), blocks of 32 x BY
+    // threads tiles of 64 x BY cells in one z-plane
+    int x0, y, z;
+    if (blockDim.y == 1) {
+        const unsigned ppr = unsigned(p.nx + 1) >> 1;
+        const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+        const unsigned row = t / ppr;
+        x0 = 2 * int(t - row * ppr);
+        y = int(row % unsigned(p.ny));
+        z = int(row / unsigned(p.ny));
+        if (z >= p.nz) return;
+    } else {
+        x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+        y = blockIdx.y * blockDim.y + threadIdx.y;
+        z = blockIdx.z;
+        if (x0 >= p.nx || y >= p.ny) return;
+    }
     const long long ps = p.ps;
 
     Geo g;

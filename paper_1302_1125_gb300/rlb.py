@@ -23,6 +23,7 @@ LIMITER_MINMOD, LIMITER_NONE = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_INLET = 0, 1, 2
 FP64, FP32_STORAGE = 0, 1
 MODEL_EXTENDED, MODEL_BASIC = 0, 1
+MAPPING_AUTO, MAPPING_TILES, MAPPING_LINEAR = 0, 1, 2   # rlb_options.thread_mapping
 Q = 19
 
 
@@ -36,7 +37,7 @@ class rlb_options(C.Structure):
     _fields_ = [("dt_over_dx", C.c_double), ("tau_override", C.c_double),
                 ("alpha_override", C.c_double), ("euler_mode", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("symmetry_1d", C.c_int),
-                ("model", C.c_int)]
+                ("model", C.c_int), ("thread_mapping", C.c_int)]
 
 
 class rlb_batch_tuning(C.Structure):
@@ -156,9 +157,11 @@ def make_grid(nx, ny=1, nz=1, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
 
 
 def make_options(dt_over_dx=0.25, tau_override=0.0, alpha_override=-1.0, euler_mode=0,
-                 precision=FP64, cuda_stream=None, symmetry_1d=0, model=MODEL_EXTENDED):
+                 precision=FP64, cuda_stream=None, symmetry_1d=0, model=MODEL_EXTENDED,
+                 thread_mapping=MAPPING_AUTO):
     return rlb_options(float(dt_over_dx), float(tau_override), float(alpha_override),
-                       int(euler_mode), int(precision), cuda_stream, int(symmetry_1d), int(model))
+                       int(euler_mode), int(precision), cuda_stream, int(symmetry_1d), int(model),
+                       int(thread_mapping))
 
 
 def rlb_check_config(grid, Q, eta_over_s, zeta_over_s, limiter, opts) -> int:
@@ -273,14 +276,14 @@ class Grid:
                  bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
                  eta_over_s=0.1, zeta_over_s=0.0, limiter=LIMITER_MINMOD, dt_over_dx=0.25,
                  tau_override=0.0, alpha_override=-1.0, euler_mode=0, precision=FP64,
-                 model=MODEL_EXTENDED, stream="current"):
+                 model=MODEL_EXTENDED, stream="current", thread_mapping=0):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = int(precision)
         s = _current_stream() if stream == "current" else stream
         self._grid = make_grid(nx, ny, nz, bc_lo, bc_hi, inlet)
         self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s,
-                                  model=model)
+                                  model=model, thread_mapping=thread_mapping)
         self.ctx = rlb_create(self._grid, Q, eta_over_s, zeta_over_s, limiter, self._opts)
 
     @classmethod

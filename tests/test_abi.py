@@ -55,7 +55,7 @@ def cfg(**kw):
         if k in g:
             g[k] = kw.pop(k)
         elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision", "symmetry_1d",
-                   "model"):
+                   "model", "thread_mapping"):
             o[k] = kw.pop(k)
     return rlb.make_grid(**g), rlb.make_options(**o), kw
 
@@ -80,6 +80,9 @@ def cfg(**kw):
     ({"dt_over_dx": -1.0}, rlb.RLB_E_INVALID),
     ({"symmetry_1d": 1}, rlb.RLB_E_INVALID),     # batched tubes only
     ({"model": 2}, rlb.RLB_E_INVALID),
+    ({"thread_mapping": 3}, rlb.RLB_E_INVALID),
+    ({"thread_mapping": -1}, rlb.RLB_E_INVALID),
+    ({"thread_mapping": 2, "ny": 8, "nz": 8}, rlb.RLB_OK),
     ({"model": 1, "dt_over_dx": 1.19}, rlb.RLB_OK),        # basic lattice, 1-D: bound sqrt(27/19) = 1.192
     ({"model": 1, "dt_over_dx": 1.2}, rlb.RLB_E_UNSTABLE),
     ({"model": 1, "ny": 8, "dt_over_dx": 0.59}, rlb.RLB_OK),   # 2-D: unit diagonals, bound 0.596

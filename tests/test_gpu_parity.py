@@ -195,6 +195,30 @@ def test_fp32_paths_l1_error_against_fp64_oracle(orc, name):
     assert max(errs) <= FP32_L1_TOL, (name, errs)
 
 
+@pytest.mark.parametrize("make", [
+    lambda: _box(37, 13, 11, 1, tau_override=0.0, alpha_override=0.1),      # odd nx: single-cell pairs
+    lambda: _box(36, 14, 10, 12, tau_override=0.0, alpha_override=0.1),
+    lambda: _all_outflow(_box(20, 12, 10, 8, tau_override=0.0, alpha_override=0.1)),
+    lambda: _box(200, 9, 1, 3, tau_override=0.0, alpha_override=0.1),       # 2-D, rows break inside warps
+    lambda: _box(128, 8, 3, 5, tau_override=0.0, alpha_override=0.1),       # tiles fill: both take every lane
+    lambda: W.sphere_cloud("beta02", scale=4, viscous=True),                # inlet face, 50 x 25 x 25
+])
+def test_fp32_thread_mappings_agree_bit_for_bit(make):
+    """tiles of 32 x 8 threads and the linear order cover the same cell
+    pairs with the same per-pair code: the states are equal bit for bit"""
+    w = make()
+    states = []
+    for mapping in (rlb.MAPPING_TILES, rlb.MAPPING_LINEAR, rlb.MAPPING_AUTO):
+        g = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE, thread_mapping=mapping)
+        g.init(*[torch.as_tensor(a, device="cuda") for a in w.fields()])
+        g.step(15)
+        states.append(g.get_state())
+        g.close()
+    for other in states[1:]:
+        for a, b in zip(states[0], other):
+            assert np.array_equal(a, b)
+
+
 @pytest.mark.parametrize("precision,tol", [(rlb.FP64, 1e-13), (rlb.FP32_STORAGE, 1e-6)])
 def test_conservation_drift(precision, tol):
     w = _box(48, 40, 1, 11, tau_override=0.8, alpha_override=0.15)
