@@ -106,14 +106,14 @@ typedef struct {
                               * (diagonals c_a, nu = sqrt(19) so c_a = 1, weights -44/361, 99/722,
                               * 9/361, number weights 1/3, 1/18, 1/36).  The step is the same
                               * (Eq. 57) on either; grids only (batched tubes: model 0). */
-    int thread_mapping;      /* FP32-storage grids of 2 or 3 dimensions: how threads (two
-                              * x-adjacent cells each) cover the grid.  0: automatic (tiles of
-                              * 32 x 8 threads when they fill at least 97 % of their lanes, else
-                              * the linear order); 1: tiles of 32 x 8 threads, i.e. 64 x 8 cells
-                              * (the better reuse of y-neighbours in L1 when nx is a multiple of
-                              * 64); 2: linear, 256 consecutive cell pairs of the x-fastest order
-                              * per block (no idle lanes when nx / 2 is not a multiple of 32).
-                              * The results are the same bit for bit. */
+    int thread_mapping;      /* grids of 2 or 3 dimensions: how threads cover the grid.  0:
+                              * automatic (tiles when they fill at least 97 % of their lanes,
+                              * else the linear order); 1: tiles (FP32 storage: 32 x 8 threads
+                              * of two x-adjacent cells each, 64 x 8 cells; FP64: 32 x 4 cells),
+                              * the better reuse of y-neighbours in L1; 2: linear, one block per
+                              * run of consecutive cells (pairs) of the x-fastest order, no idle
+                              * lanes whatever nx and ny.  The results are the same bit for
+                              * bit. */
 } rlb_options;
 
 /* Fill *opts with the defaults: dt/dx 0.25, no overrides, viscous mode, FP64,

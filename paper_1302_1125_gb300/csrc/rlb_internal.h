@@ -20,7 +20,7 @@ struct StepParams {
     double ghost_f[19], ghost_h[19];   // inlet equilibria
     unsigned *status;        // device status word (bit 0: non-physical cell)
     int lat;                 // lattice: 0 extended (Sec. II.A), 1 basic (Sec. II)
-    int mapping;             // FP32 grids: 0 automatic, 1 tiles of 32 x 8 threads, 2 linear
+    int mapping;             // grids: 0 automatic, 1 tiles, 2 linear (rlb_options.thread_mapping)
     // float copies for the FP32-storage kernel (no FP64 conversion on device)
     float f_k1, f_k2, f_half_lim, f_kw, f_kbulk, f_eta_over_s, f_tau_override;
     float f_ghost_f[19], f_ghost_h[19];

@@ -102,10 +102,23 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
                                                    const T *__restrict__ h, T *__restrict__ fo,
                                                    T *__restrict__ ho, T *__restrict__ prev)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= p.nx || y >= p.ny) return;
+    // blocks of one row of threads take consecutive cells of the x-fastest
+    // order (the 1-D form, and grids whose nx, ny do not fill the tiles),
+    // blocks of 32 x 4 threads tiles of 32 x 4 cells in one z-plane
+    int x, y, z;
+    if (blockDim.y == 1) {
+        const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+        const unsigned row = t / unsigned(p.nx);
+        x = int(t - row * unsigned(p.nx));
+        y = int(row % unsigned(p.ny));
+        z = int(row / unsigned(p.ny));
+        if (z >= p.nz) return;
+    } else {
+        x = blockIdx.x * blockDim.x + threadIdx.x;
+        y = blockIdx.y * blockDim.y + threadIdx.y;
+        z = blockIdx.z;
+        if (x >= p.nx || y >= p.ny) return;
+    }
     const int idx = x + p.nx * (y + p.ny * z);
     const long long ps = p.ps;
 

@@ -203,13 +203,14 @@ def test_fp32_paths_l1_error_against_fp64_oracle(orc, name):
     lambda: _box(128, 8, 3, 5, tau_override=0.0, alpha_override=0.1),       # tiles fill: both take every lane
     lambda: W.sphere_cloud("beta02", scale=4, viscous=True),                # inlet face, 50 x 25 x 25
 ])
-def test_fp32_thread_mappings_agree_bit_for_bit(make):
-    """tiles of 32 x 8 threads and the linear order cover the same cell
-    pairs with the same per-pair code: the states are equal bit for bit"""
+@pytest.mark.parametrize("precision", [rlb.FP32_STORAGE, rlb.FP64])
+def test_thread_mappings_agree_bit_for_bit(make, precision):
+    """tiles and the linear order cover the same cells with the same
+    per-cell code: the states are equal bit for bit"""
     w = make()
     states = []
     for mapping in (rlb.MAPPING_TILES, rlb.MAPPING_LINEAR, rlb.MAPPING_AUTO):
-        g = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE, thread_mapping=mapping)
+        g = rlb.Grid.from_workload(w, precision=precision, thread_mapping=mapping)
         g.init(*[torch.as_tensor(a, device="cuda") for a in w.fields()])
         g.step(15)
         states.append(g.get_state())
