@@ -114,6 +114,18 @@ typedef struct {
                               * run of consecutive cells (pairs) of the x-fastest order, no idle
                               * lanes whatever nx and ny.  The results are the same bit for
                               * bit. */
+    int symmetry_2d;         /* 1 (FP32-storage grids with nz = 1 < ny, viscous step): exact 2-D
+                              * symmetry reduction.  With u_z = 0 in every cell (and at the
+                              * inlet) the state is its own mirror image in z, so mirror-image
+                              * populations stay equal: 14 classes per distribution (rest, +x,
+                              * -x, +y, -y, {+z, -z}, the four x-y diagonals, (+x, +-z),
+                              * (-x, +-z), (+y, +-z), (-y, +-z)); the step updates one plane per
+                              * class (28 population planes and 4 previous-level planes instead
+                              * of 38 and 5).  rlb_init rejects a state with u_z != 0 and
+                              * rlb_set_state one whose mirror-image populations differ;
+                              * rlb_macroscopic, rlb_conserved_totals and rlb_get_state see
+                              * all 19 planes.  Results equal the 19-population step up to the
+                              * rounding order of the moment sums. */
 } rlb_options;
 
 /* Fill *opts with the defaults: dt/dx 0.25, no overrides, viscous mode, FP64,

@@ -40,6 +40,7 @@ struct rlb_ctx {
     cudaStream_t stream;
     long long launches;
     StepParams sp;
+    bool sym_stale = false;   // 2-D symmetry reduction: mirror-image planes not yet refreshed
     std::string err;
 };
 
@@ -129,6 +130,15 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.model != 0 && o.model != 1) return fail(ctx, RLB_E_INVALID, "model must be 0 (extended) or 1 (basic)");
     if (o.thread_mapping < 0 || o.thread_mapping > 2)
         return fail(ctx, RLB_E_INVALID, "thread_mapping must be 0 (automatic), 1 (tiles) or 2 (linear)");
+    if (o.symmetry_2d != 0 && o.symmetry_2d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_2d must be 0 or 1");
+    if (o.symmetry_2d) {
+        if (o.precision != RLB_FP32_STORAGE || o.euler_mode != 0)
+            return fail(ctx, RLB_E_INVALID, "symmetry_2d needs the FP32-storage form and the viscous step");
+        if (g.nz != 1 || g.ny < 2)
+            return fail(ctx, RLB_E_INVALID, "symmetry_2d needs a 2-D grid (nz = 1 < ny)");
+        if ((g.bc_lo[0] == RLB_BC_INLET || g.bc_hi[0] == RLB_BC_INLET) && g.inlet_u[2] != 0.0)
+            return fail(ctx, RLB_E_INVALID, "symmetry_2d needs inlet_u[2] = 0");
+    }
     if (!std::isfinite(o.tau_override) || !std::isfinite(o.alpha_override))
         return fail(ctx, RLB_E_INVALID, "overrides must be finite");
     // explicit stability bounds
@@ -172,11 +182,28 @@ rlb_status check_device_status(rlb_ctx *ctx, rlb_status if_bad)
     RLB_CUDA(ctx, cudaMemcpyAsync(ctx->h_status, ctx->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost,
                                   ctx->stream));
     RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (*ctx->h_status != 0u) {
+    const unsigned st = *ctx->h_status;
+    if (st != 0u) {
         RLB_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
         RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (st & rlb::ST_ASYMMETRIC)
+            return fail(ctx, RLB_E_INVALID,
+                        "symmetry_2d: the state is not its own mirror image in z (u_z != 0 or unequal populations)");
         return fail(ctx, if_bad, "a cell was non-physical (E <= |M|, n <= 0, |u| >= 1 or non-finite)");
     }
+    return RLB_OK;
+}
+
+// 2-D symmetry reduction: the step updates the class representatives only;
+// before the current level is read as 19 planes, their mirror images are
+// refreshed (one launch, skipped when nothing stepped since the last one)
+rlb_status refresh_mirrors(rlb_ctx *ctx)
+{
+    if (!ctx->sp.sym2d || !ctx->sym_stale) return RLB_OK;
+    RLB_CUDA(ctx, rlb::launch_sym2d(1, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur], (float *)ctx->hbuf[ctx->cur],
+                                    (float *)ctx->prev, ctx->d_status, ctx->stream));
+    ctx->launches += 1;
+    ctx->sym_stale = false;
     return RLB_OK;
 }
 
@@ -201,6 +228,7 @@ void rlb_default_options(rlb_options *o)
     o->symmetry_1d = 0;
     o->model = 0;
     o->thread_mapping = 0;
+    o->symmetry_2d = 0;
 }
 
 rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
@@ -296,6 +324,7 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
     sp.half_lim = limiter == RLB_LIMITER_MINMOD ? 0.5 : 0.0;
     sp.lat = o.model;
     sp.mapping = o.thread_mapping;
+    sp.sym2d = o.symmetry_2d;
     sp.k1 = lat_c0ct(o.model) * o.dt_over_dx;
     sp.k2 = double(lat_dmag(o.model)) * lat_c0ct(o.model) * o.dt_over_dx;
     sp.kw = lat_omegaC(o.model) * o.dt_over_dx;
@@ -344,8 +373,9 @@ rlb_status rlb_init(rlb_ctx *ctx, const double *n, const double *T, const double
     }
     RLB_CUDA(ctx, rlb::launch_init(ctx->fp32, ctx->N, ctx->ps, dev[0], dev[1], dev[2], dev[3], dev[4],
                                    ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur], ctx->prev, ctx->d_status,
-                                   ctx->stream, ctx->sp.lat));
+                                   ctx->stream, ctx->sp.lat, ctx->sp.sym2d));
     ctx->launches += 1;
+    ctx->sym_stale = false;
     return check_device_status(ctx, RLB_E_INVALID);
 }
 
@@ -375,6 +405,7 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
             ctx->launches += 1;
         }
     }
+    if (nsteps > 0 && ctx->sp.sym2d) ctx->sym_stale = true;
     return check_device_status(ctx, RLB_E_NONPHYSICAL);
 }
 
@@ -423,6 +454,7 @@ rlb_status rlb_macroscopic(rlb_ctx *ctx, double *out, int on_device)
     if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
     if (!out) return fail(ctx, RLB_E_INVALID, "out is NULL");
     RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (rlb_status st = refresh_mirrors(ctx); st != RLB_OK) return st;
     double *dst = on_device ? out : (double *)ctx->fbuf[1 - ctx->cur];   // 48 N bytes of staging
     RLB_CUDA(ctx, rlb::launch_macro(ctx->fp32, ctx->N, ctx->ps, ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur],
                                     dst, ctx->d_status, ctx->stream, ctx->sp.lat));
@@ -438,6 +470,7 @@ rlb_status rlb_conserved_totals(rlb_ctx *ctx, double *out)
     if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
     if (!out) return fail(ctx, RLB_E_INVALID, "out is NULL");
     RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (rlb_status st = refresh_mirrors(ctx); st != RLB_OK) return st;
     RLB_CUDA(ctx, rlb::launch_totals(ctx->fp32, ctx->N, ctx->ps, ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur],
                                      ctx->d_partial, ctx->d_tot, ctx->stream, ctx->sp.lat));
     ctx->launches += 2;
@@ -459,6 +492,9 @@ static rlb_status copy_state(rlb_ctx *ctx, void *buf, size_t bytes, bool out)
     if (!buf) return fail(ctx, RLB_E_INVALID, "buffer is NULL");
     if (bytes != rlb_state_bytes(ctx)) return fail(ctx, RLB_E_INVALID, "buffer size must equal rlb_state_bytes");
     RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (out) {
+        if (rlb_status st = refresh_mirrors(ctx); st != RLB_OK) return st;
+    }
     const size_t w = (size_t)ctx->N * ctx->esize, pitch = (size_t)ctx->ps * ctx->esize;
     char *host = (char *)buf;
     void *dev[3] = {ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur], ctx->prev};
@@ -474,6 +510,16 @@ static rlb_status copy_state(rlb_ctx *ctx, void *buf, size_t bytes, bool out)
         hoff += w * rows[k];
     }
     RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (!out && ctx->sp.sym2d) {
+        // the reduction steps the class representatives only: the state must
+        // be its own mirror image in z
+        ctx->sym_stale = false;
+        RLB_CUDA(ctx, rlb::launch_sym2d(0, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur],
+                                        (float *)ctx->hbuf[ctx->cur], (float *)ctx->prev, ctx->d_status,
+                                        ctx->stream));
+        ctx->launches += 1;
+        return check_device_status(ctx, RLB_E_INVALID);
+    }
     return RLB_OK;
 }
 

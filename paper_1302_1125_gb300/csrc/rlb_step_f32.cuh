@@ -43,26 +43,43 @@ __device__ __forceinline__ void for_pops(std::integer_sequence<int, Is...>, F &&
 }
 #define RLB_F32_POPS std::make_integer_sequence<int, 19>{}
 
-// Planes per distribution: NP = 19, or NP = 7 under the exact 1-D symmetry
-// (u_y = u_z = 0, fields uniform in y and z): then populations with the same
-// weight and the same c_x stay equal, and 7 classes remain per distribution:
-// rest, +x, -x, the four y/z axis populations, the four diagonals with
-// c_x = +2, the four with c_x = -2 and the four y-z diagonals.  Class k is
-// stored in the plane of its first population rep(k) and counts mult(k)
-// populations.
+// Planes per distribution: NP = 19, or fewer under an exact symmetry of the
+// state, when populations that the symmetry maps onto each other stay equal:
+// * NP = 7, 1-D (u_y = u_z = 0, fields uniform in y and z): populations with
+//   the same weight and the same c_x; classes rest, +x, -x, the four y/z axis
+//   populations, the four diagonals with c_x = +2, the four with c_x = -2 and
+//   the four y-z diagonals;
+// * NP = 14, 2-D (u_z = 0, fields uniform in z, i.e. nz = 1): mirror images
+//   in z; classes rest, +x, -x, +y, -y, {+z, -z}, the four x-y diagonals and
+//   the pairs (+x, +-z), (-x, +-z), (+y, +-z), (-y, +-z).
+// Class k is stored in the plane of its first population rep(k) and counts
+// mult(k) populations.
 template <int NP>
 __host__ __device__ constexpr int rep(int k)
 {
-    if constexpr (NP == 19) return k;
-    constexpr int r[7] = {0, 1, 2, 3, 7, 9, 15};
-    return r[k];
+    if constexpr (NP == 19) {
+        return k;
+    } else if constexpr (NP == 14) {
+        constexpr int r[14] = {0, 1, 2, 3, 4, 5, 7, 8, 9, 10, 11, 13, 15, 17};
+        return r[k];
+    } else {
+        constexpr int r[7] = {0, 1, 2, 3, 7, 9, 15};
+        return r[k];
+    }
 }
 template <int NP>
 __host__ __device__ constexpr int mult(int k)
 {
     if constexpr (NP == 19) return 1;
-    return k < 3 ? 1 : 4;
+    else if constexpr (NP == 14) return (k == 5 || k >= 10) ? 2 : 1;
+    else return k < 3 ? 1 : 4;
 }
+// the reduction keeps sum c_y f (NP != 7) and sum c_z f (NP == 19) only where
+// they can be non-zero
+template <int NP>
+__host__ __device__ constexpr bool has_vy() { return NP != 7; }
+template <int NP>
+__host__ __device__ constexpr bool has_vz() { return NP == 19; }
 
 // geometry of one thread's pair of cells
 struct Geo {
@@ -555,9 +572,10 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
 // populations are in flight while one is computed; stage = slot 0 of buffer
 // 0 of this thread, sstride = f2 elements between slots.
 //
-// NP = 7: the 1-D symmetry reduction (see rep and mult); only the planes of
-// the 7 class representatives are read and written, and the previous level's
-// planes of sum c_y f and sum c_z f (zero) are left alone.
+// NP = 7 or 14: the 1-D or 2-D symmetry reduction (see rep and mult); only
+// the planes of the class representatives are read and written, and the
+// previous level's planes of the zero sums (sum c_z f; 1-D also sum c_y f)
+// are left alone.
 template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false, int NP = 19,
           int LAT = 0>
 __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
@@ -569,7 +587,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
 {
     const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim;
     static_assert(!STAGE || (VEC2 && !EULER), "staging needs aligned pairs and the viscous step");
-    static_assert(NP == 19 || (NP == 7 && DIM == 1 && !EULER), "the symmetry reduction is 1-D, viscous");
+    static_assert(NP == 19 || (NP == 7 && DIM == 1 && !EULER) || (NP == 14 && DIM == 2 && !EULER),
+                  "the symmetry reductions are 1-D or 2-D and viscous");
     constexpr int NI = 2 * NP;   // items: f classes, then h classes
     unsigned sdst0 = 0;
     if constexpr (STAGE) {
@@ -616,10 +635,9 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
             acc(S, scaled(std::integral_constant<int, m>{}));
             constexpr int cx = cdir<I, 0, LAT>(), cy = cdir<I, 1, LAT>(), cz = cdir<I, 2, LAT>();
             if constexpr (cx != 0) acc(Vx, scaled(std::integral_constant<int, cx * m>{}));
-            if constexpr (NP == 19) {   // under the reduction sum c_y f = sum c_z f = 0
-                if constexpr (cy != 0) acc(Vy, scaled(std::integral_constant<int, cy>{}));
-                if constexpr (cz != 0) acc(Vz, scaled(std::integral_constant<int, cz>{}));
-            }
+            // under a reduction sum c_y f (1-D) and sum c_z f are zero
+            if constexpr (has_vy<NP>() && cy != 0) acc(Vy, scaled(std::integral_constant<int, cy * m>{}));
+            if constexpr (has_vz<NP>() && cz != 0) acc(Vz, scaled(std::integral_constant<int, cz * m>{}));
             const f2 hv = ldpair<VEC2, LD>(h + I * ps, g, 0);
             acc(Hs, m == 1 ? hv : bc(float(m)) * hv);
         });
@@ -646,8 +664,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         // targets of 2 f^eq(t) - f^eq(t - dt) are exact: T = 2 S(t) - S(t - dt)
         const f2 Sp = ldpair<VEC2, LD>(prev + 0 * ps, g, 0);
         const f2 Vpx = ldpair<VEC2, LD>(prev + 1 * ps, g, 0);
-        const f2 Vpy = NP == 19 ? ldpair<VEC2, LD>(prev + 2 * ps, g, 0) : bc(0.0f);
-        const f2 Vpz = NP == 19 ? ldpair<VEC2, LD>(prev + 3 * ps, g, 0) : bc(0.0f);
+        const f2 Vpy = has_vy<NP>() ? ldpair<VEC2, LD>(prev + 2 * ps, g, 0) : bc(0.0f);
+        const f2 Vpz = has_vz<NP>() ? ldpair<VEC2, LD>(prev + 3 * ps, g, 0) : bc(0.0f);
         const f2 Shp = ldpair<VEC2, LD>(prev + 4 * ps, g, 0);
         const Mac2 mp = recover2f<LAT>(Sp, Vpx, Vpy, Vpz, Shp);
         const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
@@ -687,10 +705,8 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
             // the raw sums of this level become the next step's previous level
             stpair<VEC2>(prev + 0 * ps, g, S.hi + S.lo);
             stpair<VEC2>(prev + 1 * ps, g, Vx.hi + Vx.lo);
-            if constexpr (NP == 19) {
-                stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
-                stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
-            }
+            if constexpr (has_vy<NP>()) stpair<VEC2>(prev + 2 * ps, g, Vy.hi + Vy.lo);
+            if constexpr (has_vz<NP>()) stpair<VEC2>(prev + 3 * ps, g, Vz.hi + Vz.lo);
             stpair<VEC2>(prev + 4 * ps, g, Sh);
             if constexpr (PARK) {
                 park[0] = H0;
@@ -787,18 +803,19 @@ constexpr size_t step_smem_bytes(int nthr, bool stage, int dim)
     return sizeof(f2) * size_t(nthr) * ((kParkOn ? kParkSlots : 0) + (stage ? 3 * dim * kStageBufs : 0));
 }
 
-template <int DIM, bool EULER, bool VEC2, int LAT>
+// NP = 14: the 2-D symmetry reduction (DIM = 2, viscous step).  LIN: blocks
+// of one row of 32 BY threads take consecutive cell pairs t of the x-fastest
+// order (rows of ceil(nx / 2) pairs), for grids whose nx does not fill the
+// tiles; otherwise blocks of 32 x BY threads take tiles of 64 x BY cells in
+// one z-plane (the 1-D form: one row of tiles)
+template <int DIM, bool EULER, bool VEC2, int LAT, int NP = 19, bool LIN = false>
 __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
     step_f32_kernel(const StepParams p, const float *__restrict__ f, const float *__restrict__ h,
                     float *__restrict__ fo, float *__restrict__ ho, float *__restrict__ prev)
 {
     extern __shared__ f2 s_park[];
-    // the block shape gives the mapping: blocks of one row take consecutive
-    // pairs t of the x-fastest order (rows of ceil(nx / 2) pairs; the 1-D
-    // form, and grids whose nx does not fill the tiles), blocks of 32 x BY
-    // threads tiles of 64 x BY cells in one z-plane
     int x0, y, z;
-    if (blockDim.y == 1) {
+    if constexpr (LIN) {
         const unsigned ppr = unsigned(p.nx + 1) >> 1;
         const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
         const unsigned row = t / ppr;
@@ -844,7 +861,7 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
     const int nthr = blockDim.x * blockDim.y;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     constexpr bool STAGE = kStageOn && VEC2 && !EULER;
-    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE, 19, LAT>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho,
+    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE, NP, LAT>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho,
                                                                   prev, ps,
                                                          s_park + tid, nthr,
                                                          s_park + (kParkOn ? kParkSlots * nthr : 0) + tid, nthr);

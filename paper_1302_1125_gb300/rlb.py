@@ -37,7 +37,7 @@ class rlb_options(C.Structure):
     _fields_ = [("dt_over_dx", C.c_double), ("tau_override", C.c_double),
                 ("alpha_override", C.c_double), ("euler_mode", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("symmetry_1d", C.c_int),
-                ("model", C.c_int), ("thread_mapping", C.c_int)]
+                ("model", C.c_int), ("thread_mapping", C.c_int), ("symmetry_2d", C.c_int)]
 
 
 class rlb_batch_tuning(C.Structure):
@@ -158,10 +158,10 @@ def make_grid(nx, ny=1, nz=1, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
 
 def make_options(dt_over_dx=0.25, tau_override=0.0, alpha_override=-1.0, euler_mode=0,
                  precision=FP64, cuda_stream=None, symmetry_1d=0, model=MODEL_EXTENDED,
-                 thread_mapping=MAPPING_AUTO):
+                 thread_mapping=MAPPING_AUTO, symmetry_2d=0):
     return rlb_options(float(dt_over_dx), float(tau_override), float(alpha_override),
                        int(euler_mode), int(precision), cuda_stream, int(symmetry_1d), int(model),
-                       int(thread_mapping))
+                       int(thread_mapping), int(symmetry_2d))
 
 
 def rlb_check_config(grid, Q, eta_over_s, zeta_over_s, limiter, opts) -> int:
@@ -276,14 +276,14 @@ class Grid:
                  bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
                  eta_over_s=0.1, zeta_over_s=0.0, limiter=LIMITER_MINMOD, dt_over_dx=0.25,
                  tau_override=0.0, alpha_override=-1.0, euler_mode=0, precision=FP64,
-                 model=MODEL_EXTENDED, stream="current", thread_mapping=0):
+                 model=MODEL_EXTENDED, stream="current", thread_mapping=0, symmetry_2d=0):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = int(precision)
         s = _current_stream() if stream == "current" else stream
         self._grid = make_grid(nx, ny, nz, bc_lo, bc_hi, inlet)
         self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s,
-                                  model=model, thread_mapping=thread_mapping)
+                                  model=model, thread_mapping=thread_mapping, symmetry_2d=symmetry_2d)
         self.ctx = rlb_create(self._grid, Q, eta_over_s, zeta_over_s, limiter, self._opts)
 
     @classmethod
@@ -347,6 +347,7 @@ class Grid:
         buf = np.ascontiguousarray(np.concatenate([np.ravel(f), np.ravel(h), np.ravel(prev)]),
                                    self.state_dtype())
         rlb_set_state(self.ctx, buf, 0)
+        return self
 
     @property
     def launches(self) -> int:

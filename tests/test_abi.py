@@ -55,7 +55,7 @@ def cfg(**kw):
         if k in g:
             g[k] = kw.pop(k)
         elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision", "symmetry_1d",
-                   "model", "thread_mapping"):
+                   "model", "thread_mapping", "symmetry_2d"):
             o[k] = kw.pop(k)
     return rlb.make_grid(**g), rlb.make_options(**o), kw
 
@@ -83,6 +83,16 @@ def cfg(**kw):
     ({"thread_mapping": 3}, rlb.RLB_E_INVALID),
     ({"thread_mapping": -1}, rlb.RLB_E_INVALID),
     ({"thread_mapping": 2, "ny": 8, "nz": 8}, rlb.RLB_OK),
+    ({"symmetry_2d": 1, "ny": 8, "precision": 1}, rlb.RLB_OK),
+    ({"symmetry_2d": 2, "ny": 8, "precision": 1}, rlb.RLB_E_INVALID),
+    ({"symmetry_2d": 1, "ny": 8}, rlb.RLB_E_INVALID),                       # FP32 storage only
+    ({"symmetry_2d": 1, "ny": 8, "precision": 1, "euler_mode": 1}, rlb.RLB_E_INVALID),
+    ({"symmetry_2d": 1, "precision": 1}, rlb.RLB_E_INVALID),                # 1-D grid
+    ({"symmetry_2d": 1, "ny": 8, "nz": 4, "precision": 1}, rlb.RLB_E_INVALID),   # 3-D grid
+    ({"symmetry_2d": 1, "ny": 8, "precision": 1, "bc_lo": (2, 0, 0),
+      "inlet": (1.0, 1.0, (0.5, 0.0, 0.1))}, rlb.RLB_E_INVALID),            # inlet moving in z
+    ({"symmetry_2d": 1, "ny": 8, "precision": 1, "bc_lo": (2, 0, 0),
+      "inlet": (1.0, 1.0, (0.5, 0.3, 0.0))}, rlb.RLB_OK),
     ({"model": 1, "dt_over_dx": 1.19}, rlb.RLB_OK),        # basic lattice, 1-D: bound sqrt(27/19) = 1.192
     ({"model": 1, "dt_over_dx": 1.2}, rlb.RLB_E_UNSTABLE),
     ({"model": 1, "ny": 8, "dt_over_dx": 0.59}, rlb.RLB_OK),   # 2-D: unit diagonals, bound 0.596
