@@ -97,16 +97,17 @@ __device__ __forceinline__ void flag(const StepParams &p, unsigned bits)
     atomicOr(p.status, bits);
 }
 
-template <typename T, int DIM, bool EULER, int LAT>
+// LIN: blocks of one row of threads take consecutive cells of the x-fastest
+// order (grids whose nx, ny do not fill the tiles); otherwise blocks of
+// 32 x 4 threads take tiles of 32 x 4 cells in one z-plane (the 1-D form:
+// one row of tiles)
+template <typename T, int DIM, bool EULER, int LAT, bool LIN = false>
 __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *__restrict__ f,
                                                    const T *__restrict__ h, T *__restrict__ fo,
                                                    T *__restrict__ ho, T *__restrict__ prev)
 {
-    // blocks of one row of threads take consecutive cells of the x-fastest
-    // order (the 1-D form, and grids whose nx, ny do not fill the tiles),
-    // blocks of 32 x 4 threads tiles of 32 x 4 cells in one z-plane
     int x, y, z;
-    if (blockDim.y == 1) {
+    if constexpr (LIN) {
         const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
         const unsigned row = t / unsigned(p.nx);
         x = int(t - row * unsigned(p.nx));

@@ -10,26 +10,21 @@ template <typename T, int DIM, bool EULER, int LAT>
 cudaError_t launch_step_t(const StepParams &p, const T *f, const T *h, T *fo, T *ho, T *prev,
                           cudaStream_t s)
 {
-    dim3 block, grid;
     if (DIM == 1) {
-        block = dim3(128, 1, 1);
-        grid = dim3((p.nx + 127) / 128, 1, 1);
-    } else {
-        // tiles of 32 x 4 cells when nx and ny fill them, else 128 consecutive
-        // cells of the x-fastest order per block (the kernel reads the mapping
-        // from the block shape)
-        const long long tiles_x = (p.nx + 31) / 32, tiles_y = (p.ny + 3) / 4;
-        const long long cells = (long long)p.nx * p.ny * p.nz;
-        const double fill = double(p.nx) * p.ny / double(tiles_x * 32 * tiles_y * 4);
-        if (p.mapping == 2 || (p.mapping == 0 && fill < 0.97)) {
-            block = dim3(128, 1, 1);
-            grid = dim3(unsigned((cells + 127) / 128), 1, 1);
-        } else {
-            block = dim3(32, 4, 1);
-            grid = dim3(unsigned(tiles_x), unsigned(tiles_y), p.nz);
-        }
+        step_kernel<T, DIM, EULER, LAT><<<(p.nx + 127) / 128, 128, 0, s>>>(p, f, h, fo, ho, prev);
+        return cudaGetLastError();
     }
-    step_kernel<T, DIM, EULER, LAT><<<grid, block, 0, s>>>(p, f, h, fo, ho, prev);
+    // tiles of 32 x 4 cells when nx and ny fill them, else 128 consecutive
+    // cells of the x-fastest order per block
+    const long long tiles_x = (p.nx + 31) / 32, tiles_y = (p.ny + 3) / 4;
+    const long long cells = (long long)p.nx * p.ny * p.nz;
+    const double fill = double(p.nx) * p.ny / double(tiles_x * 32 * tiles_y * 4);
+    if (p.mapping == 2 || (p.mapping == 0 && fill < 0.97)) {
+        step_kernel<T, DIM, EULER, LAT, true><<<unsigned((cells + 127) / 128), 128, 0, s>>>(p, f, h, fo, ho, prev);
+    } else {
+        const dim3 grid(unsigned(tiles_x), unsigned(tiles_y), p.nz);
+        step_kernel<T, DIM, EULER, LAT, false><<<grid, dim3(32, 4, 1), 0, s>>>(p, f, h, fo, ho, prev);
+    }
     return cudaGetLastError();
 }
 
