@@ -157,7 +157,14 @@ RLB_API rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, do
 /* Initialise the populations to equilibrium: f = f^eq(P = n T, u) (Eq. 36 with
  * Eq. 38), h = h^eq(n, u) (Eq. 58), and the previous level to the same state
  * (so the first step uses f^eq(-dt) = f^eq(0)).  n, T, ux, uy, uz: N doubles
- * each (three-velocity components, |u| < 1).  Synchronous. */
+ * each (three-velocity components, |u| < 1), host or device memory per
+ * on_device.  The FP64 form evaluates the equilibria in double; the
+ * FP32-storage form in float from n T, n, u and 1 - |u|^2 rounded to float
+ * (each population within a few float roundings of its double value), so it
+ * also rejects states whose n, n T or 1 - |u|^2 fall outside the float range.
+ * RLB_E_INVALID (the context stays usable) if a cell has n <= 0, T <= 0,
+ * |u| >= 1 or a non-finite value, or, under symmetry_2d, u_z != 0.
+ * Synchronous. */
 RLB_API rlb_status rlb_init(rlb_ctx *ctx, const double *n, const double *T, const double *ux,
                     const double *uy, const double *uz, int on_device);
 
