@@ -161,3 +161,20 @@ def test_set_state_checks_the_symmetry():
         assert np.array_equal(a, b)
     g.close()
     g2.close()
+
+
+def test_full_size_cloud_2d_reduced_equals_full():
+    """the benchmark's 2048 x 1024 2-D shock-cloud: 40 steps with and without
+    the reduction, compared over the whole grid"""
+    w = W.cloud_2d()
+    full = run(w, 40, 0)
+    red = run(w, 40, 1)
+    mf, mr = full.macroscopic(device=False), red.macroscopic(device=False)
+    for k in (0, 1, 5):
+        assert l1rel(mr[k], mf[k]) <= 1e-6, k
+        assert np.abs(mr[k] - mf[k]).max() <= 1e-5 * np.abs(mf[k]).max(), k
+    for k in (2, 3):
+        assert np.abs(mr[k] - mf[k]).sum() / np.abs(mf[5]).sum() <= 1e-6, k
+    assert np.abs(mr[4]).max() == 0.0
+    full.close()
+    red.close()
