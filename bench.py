@@ -540,17 +540,26 @@ def run_ours(args):
     ge.init(*[a.numpy() for a in host_in]).step(args.warmup)
     torch.cuda.synchronize()
     barrier()
-    t0 = time.perf_counter()
-    ge.init(*[a.numpy() for a in host_in])
-    ge.step(args.steps)
-    rlb.rlb_macroscopic(ge.ctx, host_out.numpy(), 0)
-    torch.cuda.synchronize()
-    e2e_s = max_over_ranks(torch, time.perf_counter() - t0)
+    # each call returns after its work (rlb_init, rlb_step and rlb_macroscopic
+    # synchronise), so the wall clock splits into the three phases
+    with ClockSampler(local) as cs_e2e:
+        t0 = time.perf_counter()
+        ge.init(*[a.numpy() for a in host_in])
+        t1 = time.perf_counter()
+        ge.step(args.steps)
+        t2 = time.perf_counter()
+        rlb.rlb_macroscopic(ge.ctx, host_out.numpy(), 0)
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+    e2e_s = max_over_ranks(torch, t3 - t0)
     barrier()
     ge.close()
     e2e = {"value": world * N * args.steps / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": 5 * 8 * N / args.steps, "d2h_bytes_per_step": 6 * 8 * N / args.steps,
-           "what": "pinned host n,T,u -> rlb_init -> K steps -> rlb_macroscopic to pinned host"}
+           "what": "pinned host n,T,u -> rlb_init -> K steps -> rlb_macroscopic to pinned host",
+           "phases_ms": {"init_from_host": 1e3 * (t1 - t0), "steps": 1e3 * (t2 - t1),
+                         "output_to_host": 1e3 * (t3 - t2)},
+           "clocks": cs_e2e.summary()}
 
     batch = batch_sweep(torch, rlb, W, hbm_peak, local) if not args.no_batch else None
     sphere = sphere_run(torch, rlb, W, local) if not args.no_batch else None
