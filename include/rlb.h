@@ -93,14 +93,19 @@ typedef struct {
     int euler_mode;          /* 1: f <- f^eq, h <- h^eq of the streamed state (Sec. III) */
     int precision;           /* RLB_FP64 or RLB_FP32_STORAGE */
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
-    int symmetry_1d;         /* 1 (batched tubes only): exact 1-D symmetry reduction.  With
+    int symmetry_1d;         /* 1: exact 1-D symmetry reduction, for batched tubes and for
+                              * FP32-storage grids with ny = nz = 1 (viscous step).  With
                               * u_y = u_z = 0 and fields uniform in y and z, populations with
                               * the same weight and the same c_x stay equal, leaving 7 classes
                               * per distribution (rest, +x, -x, the y/z axis populations, the
                               * diagonals with c_x = +2, with c_x = -2, the y-z diagonals); the
                               * step updates one plane per class (14 population planes and 3
-                              * previous-level planes instead of 38 and 5).  Results equal the
-                              * 19-population step up to the rounding order of the moment sums. */
+                              * previous-level planes instead of 38 and 5).  On a grid
+                              * rlb_init rejects u_y or u_z != 0 and rlb_set_state a state
+                              * whose class members differ; rlb_macroscopic,
+                              * rlb_conserved_totals and rlb_get_state see all 19 planes.
+                              * Results equal the 19-population step up to the rounding order
+                              * of the moment sums. */
     int model;               /* lattice: 0 the extended D3Q19 configuration (Sec. II.A, diagonals
                               * 2 c_a, nu = sqrt(13)); 1 the basic D3Q19 lattice of Sec. II
                               * (diagonals c_a, nu = sqrt(19) so c_a = 1, weights -44/361, 99/722,

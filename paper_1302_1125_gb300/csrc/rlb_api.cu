@@ -125,12 +125,20 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.precision != RLB_FP64 && o.precision != RLB_FP32_STORAGE)
         return fail(ctx, RLB_E_INVALID, "unknown precision");
     if (o.euler_mode != 0 && o.euler_mode != 1) return fail(ctx, RLB_E_INVALID, "euler_mode must be 0 or 1");
-    if (o.symmetry_1d != 0)
-        return fail(ctx, RLB_E_INVALID, "the 1-D symmetry reduction is available for batched tubes (rlb_batch_create)");
+    if (o.symmetry_1d != 0 && o.symmetry_1d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_1d must be 0 or 1");
+    if (o.symmetry_1d) {
+        if (o.precision != RLB_FP32_STORAGE || o.euler_mode != 0)
+            return fail(ctx, RLB_E_INVALID, "symmetry_1d needs the FP32-storage form and the viscous step");
+        if (g.ny != 1 || g.nz != 1)
+            return fail(ctx, RLB_E_INVALID, "symmetry_1d on a grid needs a 1-D grid (ny = nz = 1)");
+        if ((g.bc_lo[0] == RLB_BC_INLET || g.bc_hi[0] == RLB_BC_INLET) && (g.inlet_u[1] != 0.0 || g.inlet_u[2] != 0.0))
+            return fail(ctx, RLB_E_INVALID, "symmetry_1d needs inlet_u[1] = inlet_u[2] = 0");
+    }
     if (o.model != 0 && o.model != 1) return fail(ctx, RLB_E_INVALID, "model must be 0 (extended) or 1 (basic)");
     if (o.thread_mapping < 0 || o.thread_mapping > 2)
         return fail(ctx, RLB_E_INVALID, "thread_mapping must be 0 (automatic), 1 (tiles) or 2 (linear)");
     if (o.symmetry_2d != 0 && o.symmetry_2d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_2d must be 0 or 1");
+    if (o.symmetry_1d && o.symmetry_2d) return fail(ctx, RLB_E_INVALID, "symmetry_1d and symmetry_2d exclude each other");
     if (o.symmetry_2d) {
         if (o.precision != RLB_FP32_STORAGE || o.euler_mode != 0)
             return fail(ctx, RLB_E_INVALID, "symmetry_2d needs the FP32-storage form and the viscous step");
@@ -188,20 +196,22 @@ rlb_status check_device_status(rlb_ctx *ctx, rlb_status if_bad)
         RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
         if (st & rlb::ST_ASYMMETRIC)
             return fail(ctx, RLB_E_INVALID,
-                        "symmetry_2d: the state is not its own mirror image in z (u_z != 0 or unequal populations)");
+                        "symmetry reduction: the state is not its own mirror image (u_y or u_z != 0, or unequal "
+                        "populations in a class)");
         return fail(ctx, if_bad, "a cell was non-physical (E <= |M|, n <= 0, |u| >= 1 or non-finite)");
     }
     return RLB_OK;
 }
 
-// 2-D symmetry reduction: the step updates the class representatives only;
-// before the current level is read as 19 planes, their mirror images are
-// refreshed (one launch, skipped when nothing stepped since the last one)
+// symmetry reductions: the step updates the class representatives only;
+// before the current level is read as 19 planes, the other members of each
+// class are refreshed (one launch, skipped when nothing stepped since the
+// last one)
 rlb_status refresh_mirrors(rlb_ctx *ctx)
 {
-    if (!ctx->sp.sym2d || !ctx->sym_stale) return RLB_OK;
-    RLB_CUDA(ctx, rlb::launch_sym2d(1, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur], (float *)ctx->hbuf[ctx->cur],
-                                    (float *)ctx->prev, ctx->d_status, ctx->stream));
+    if (!ctx->sp.sym || !ctx->sym_stale) return RLB_OK;
+    RLB_CUDA(ctx, rlb::launch_sym(1, ctx->sp.sym, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur],
+                                  (float *)ctx->hbuf[ctx->cur], (float *)ctx->prev, ctx->d_status, ctx->stream));
     ctx->launches += 1;
     ctx->sym_stale = false;
     return RLB_OK;
@@ -324,7 +334,7 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
     sp.half_lim = limiter == RLB_LIMITER_MINMOD ? 0.5 : 0.0;
     sp.lat = o.model;
     sp.mapping = o.thread_mapping;
-    sp.sym2d = o.symmetry_2d;
+    sp.sym = o.symmetry_1d ? 1 : (o.symmetry_2d ? 2 : 0);
     sp.k1 = lat_c0ct(o.model) * o.dt_over_dx;
     sp.k2 = double(lat_dmag(o.model)) * lat_c0ct(o.model) * o.dt_over_dx;
     sp.kw = lat_omegaC(o.model) * o.dt_over_dx;
@@ -373,7 +383,7 @@ rlb_status rlb_init(rlb_ctx *ctx, const double *n, const double *T, const double
     }
     RLB_CUDA(ctx, rlb::launch_init(ctx->fp32, ctx->N, ctx->ps, dev[0], dev[1], dev[2], dev[3], dev[4],
                                    ctx->fbuf[ctx->cur], ctx->hbuf[ctx->cur], ctx->prev, ctx->d_status,
-                                   ctx->stream, ctx->sp.lat, ctx->sp.sym2d));
+                                   ctx->stream, ctx->sp.lat, ctx->sp.sym));
     ctx->launches += 1;
     ctx->sym_stale = false;
     return check_device_status(ctx, RLB_E_INVALID);
@@ -405,7 +415,7 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
             ctx->launches += 1;
         }
     }
-    if (nsteps > 0 && ctx->sp.sym2d) ctx->sym_stale = true;
+    if (nsteps > 0 && ctx->sp.sym) ctx->sym_stale = true;
     return check_device_status(ctx, RLB_E_NONPHYSICAL);
 }
 
@@ -510,13 +520,13 @@ static rlb_status copy_state(rlb_ctx *ctx, void *buf, size_t bytes, bool out)
         hoff += w * rows[k];
     }
     RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    if (!out && ctx->sp.sym2d) {
-        // the reduction steps the class representatives only: the state must
-        // be its own mirror image in z
+    if (!out && ctx->sp.sym) {
+        // a reduction steps the class representatives only: every member of
+        // a class must equal its representative
         ctx->sym_stale = false;
-        RLB_CUDA(ctx, rlb::launch_sym2d(0, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur],
-                                        (float *)ctx->hbuf[ctx->cur], (float *)ctx->prev, ctx->d_status,
-                                        ctx->stream));
+        RLB_CUDA(ctx, rlb::launch_sym(0, ctx->sp.sym, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur],
+                                      (float *)ctx->hbuf[ctx->cur], (float *)ctx->prev, ctx->d_status,
+                                      ctx->stream));
         ctx->launches += 1;
         return check_device_status(ctx, RLB_E_INVALID);
     }

@@ -42,34 +42,41 @@ __global__ void solid_reset_kernel(int M, const int *__restrict__ idx, long long
 
 // FP32-storage forms of the three kernels above, two cells per thread in
 // float arithmetic (rlb_cellops_f32.cuh): consecutive cells i0 = 2 t, i0 + 1
-// (sym2d: the state must have u_z = 0 for the 2-D symmetry reduction)
+// (sym: the state must have u_y = u_z = 0 for the 1-D symmetry reduction,
+// u_z = 0 for the 2-D one)
 template <int LAT>
 __global__ void init_kernel_f32(int N, long long ps, const double *__restrict__ n, const double *__restrict__ Tt,
                                 const double *__restrict__ ux, const double *__restrict__ uy,
                                 const double *__restrict__ uz, float *__restrict__ f, float *__restrict__ h,
-                                float *__restrict__ prev, unsigned *status, int sym2d)
+                                float *__restrict__ prev, unsigned *status, int sym)
 {
     const long long i0 = 2LL * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
     if (i0 >= N) return;
     const bool has1 = i0 + 1 < N;
     const long long i1 = has1 ? i0 + 1 : i0;
-    if (sym2d && (uz[i0] != 0.0 || uz[i1] != 0.0)) atomicOr(status, unsigned(ST_ASYMMETRIC));
+    if (sym && (uz[i0] != 0.0 || uz[i1] != 0.0 || (sym == 1 && (uy[i0] != 0.0 || uy[i1] != 0.0))))
+        atomicOr(status, unsigned(ST_ASYMMETRIC));
     f32::init_pair<LAT, true>(f32::CellPair{i0, i1, i0, i1, has1}, ps, n, Tt, ux, uy, uz, f, h, prev, status);
 }
 
-// the 2-D symmetry reduction's mirror images in z: population kMirror[j][1]
-// is the image of the class representative kMirror[j][0]
-__constant__ int kMirror[5][2] = {{5, 6}, {11, 12}, {13, 14}, {15, 16}, {17, 18}};
+// the members of the reductions' classes: population kMember[j][1] equals
+// its class representative kMember[j][0].  2-D (the first 5): mirror images
+// in z.  1-D (all 12): the y/z axis populations, the diagonals with
+// c_x = +2, those with c_x = -2, the y-z diagonals (the classes of the
+// batched-tube reduction).
+__constant__ int kMember[2][12][2] = {
+    {{3, 4}, {3, 5}, {3, 6}, {7, 8}, {7, 11}, {7, 12}, {9, 10}, {9, 13}, {9, 14}, {15, 16}, {15, 17}, {15, 18}},
+    {{5, 6}, {11, 12}, {13, 14}, {15, 16}, {17, 18}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}}};
 
-__global__ void sym2d_kernel(int expand, int N, long long ps, float *__restrict__ f, float *__restrict__ h,
-                             float *__restrict__ prev, unsigned *status)
+__global__ void sym_kernel(int expand, int sym, int N, long long ps, float *__restrict__ f, float *__restrict__ h,
+                           float *__restrict__ prev, unsigned *status)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
+    const int t = sym == 1 ? 0 : 1, m = sym == 1 ? 12 : 5;
     bool same = true;
-#pragma unroll
-    for (int j = 0; j < 5; ++j) {
-        const long long a = kMirror[j][0] * ps + i, b = kMirror[j][1] * ps + i;
+    for (int j = 0; j < m; ++j) {
+        const long long a = kMember[t][j][0] * ps + i, b = kMember[t][j][1] * ps + i;
         if (expand) {
             f[b] = f[a];
             h[b] = h[a];
@@ -77,8 +84,12 @@ __global__ void sym2d_kernel(int expand, int N, long long ps, float *__restrict_
             same = same && f[b] == f[a] && h[b] == h[a];
         }
     }
-    if (expand) prev[3 * ps + i] = 0.0f;
-    else if (!same) atomicOr(status, unsigned(ST_ASYMMETRIC));
+    if (expand) {
+        if (sym == 1) prev[2 * ps + i] = 0.0f;
+        prev[3 * ps + i] = 0.0f;
+    } else if (!same) {
+        atomicOr(status, unsigned(ST_ASYMMETRIC));
+    }
 }
 
 template <int LAT>
@@ -154,24 +165,25 @@ __global__ void totals_finish(int nblocks, const double *__restrict__ partial, d
 }
 
 
-cudaError_t launch_sym2d(int expand, int N, long long ps, float *f, float *h, float *prev, unsigned *status,
-                         cudaStream_t s)
+cudaError_t launch_sym(int expand, int sym, int N, long long ps, float *f, float *h, float *prev,
+                       unsigned *status, cudaStream_t s)
 {
+    if (sym != 1 && sym != 2) return cudaErrorInvalidValue;
     const int b = 256, g = (N + b - 1) / b;
-    sym2d_kernel<<<g, b, 0, s>>>(expand, N, ps, f, h, prev, status);
+    sym_kernel<<<g, b, 0, s>>>(expand, sym, N, ps, f, h, prev, status);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const double *T,
                         const double *ux, const double *uy, const double *uz, void *f, void *h,
-                        void *prev, unsigned *status, cudaStream_t s, int lat, int sym2d)
+                        void *prev, unsigned *status, cudaStream_t s, int lat, int sym)
 {
     const int b = 128, g = (N + b - 1) / b, g2 = (N + 2 * b - 1) / (2 * b);
     auto go = [&](auto lc) {
         constexpr int L = decltype(lc)::value;
         if (fp32)
             init_kernel_f32<L><<<g2, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (float *)f, (float *)h, (float *)prev,
-                                                status, sym2d);
+                                                status, sym);
         else
             init_kernel<double, L><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (double *)f, (double *)h,
                                                    (double *)prev, status);

@@ -27,7 +27,10 @@ cudaError_t launch_f32(const StepParams &p, const float *f, const float *h, floa
                        cudaStream_t s)
 {
     if constexpr (DIM == 2 && !EULER && NP == 19) {
-        if (p.sym2d) return launch_f32<2, false, VEC2, LAT, 14, LIN>(p, f, h, fo, ho, prev, s);
+        if (p.sym == 2) return launch_f32<2, false, VEC2, LAT, 14, LIN>(p, f, h, fo, ho, prev, s);
+    }
+    if constexpr (DIM == 1 && !EULER && NP == 19 && !LIN) {
+        if (p.sym == 1) return launch_f32<1, false, VEC2, LAT, 7, false>(p, f, h, fo, ho, prev, s);
     }
     const int npairs = (p.nx + 1) / 2;
     dim3 block, grid;

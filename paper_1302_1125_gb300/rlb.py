@@ -276,14 +276,15 @@ class Grid:
                  bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
                  eta_over_s=0.1, zeta_over_s=0.0, limiter=LIMITER_MINMOD, dt_over_dx=0.25,
                  tau_override=0.0, alpha_override=-1.0, euler_mode=0, precision=FP64,
-                 model=MODEL_EXTENDED, stream="current", thread_mapping=0, symmetry_2d=0):
+                 model=MODEL_EXTENDED, stream="current", thread_mapping=0, symmetry_1d=0, symmetry_2d=0):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = int(precision)
         s = _current_stream() if stream == "current" else stream
         self._grid = make_grid(nx, ny, nz, bc_lo, bc_hi, inlet)
         self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s,
-                                  model=model, thread_mapping=thread_mapping, symmetry_2d=symmetry_2d)
+                                  symmetry_1d=symmetry_1d, model=model, thread_mapping=thread_mapping,
+                                  symmetry_2d=symmetry_2d)
         self.ctx = rlb_create(self._grid, Q, eta_over_s, zeta_over_s, limiter, self._opts)
 
     @classmethod

@@ -78,7 +78,13 @@ def cfg(**kw):
     ({"alpha_override": 1.0}, rlb.RLB_E_UNSTABLE),       # 2 (c0 nu/ct) dt alpha > 1
     ({"alpha_override": 0.5}, rlb.RLB_OK),
     ({"dt_over_dx": -1.0}, rlb.RLB_E_INVALID),
-    ({"symmetry_1d": 1}, rlb.RLB_E_INVALID),     # batched tubes only
+    ({"symmetry_1d": 1}, rlb.RLB_E_INVALID),     # FP32 storage only
+    ({"symmetry_1d": 1, "precision": 1}, rlb.RLB_OK),
+    ({"symmetry_1d": 1, "precision": 1, "ny": 8}, rlb.RLB_E_INVALID),     # 1-D grids only
+    ({"symmetry_1d": 1, "precision": 1, "euler_mode": 1}, rlb.RLB_E_INVALID),
+    ({"symmetry_1d": 1, "symmetry_2d": 1, "precision": 1, "ny": 8}, rlb.RLB_E_INVALID),
+    ({"symmetry_1d": 1, "precision": 1, "bc_lo": (2, 0, 0),
+      "inlet": (1.0, 1.0, (0.5, 0.1, 0.0))}, rlb.RLB_E_INVALID),          # inlet moving in y
     ({"model": 2}, rlb.RLB_E_INVALID),
     ({"thread_mapping": 3}, rlb.RLB_E_INVALID),
     ({"thread_mapping": -1}, rlb.RLB_E_INVALID),
