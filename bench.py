@@ -435,6 +435,55 @@ def cloud_2d_run(torch, rlb, W, hbm_peak, steps=200):
     return out
 
 
+def paper_runs(torch, rlb, W):
+    """The paper's timed 1-D runs (Sec. III: 800 cells, dt/dx 0.25, t = 3.2 fm,
+    i.e. 1600 steps), each as a whole run through the public API with host
+    arrays: rlb_init from host fields, the steps, rlb_macroscopic to host.
+    Next to them the oracle, as it stands, on the same run on the host cores,
+    and the paper's own wall times (an unnamed "standard PC"; context only)."""
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
+    cases = [
+        ("P ratio 5.43/2.22, T ratio 2, eta/s 0.1, alpha 0 (beta ~ 0.2)", 5.43 / 2.22, 0.1, 0.0, 220.0),
+        ("P ratio 32, T ratio 2, eta/s 0.01, alpha 0.15, extended model (beta ~ 0.7)", 32.0, 0.01, 0.15, 1069.0),
+    ]
+    out = {"what": "the paper's timed 1-D runs: 800 cells, dt/dx 0.25, 1600 steps; wall time of the whole run "
+                   "(init from host, steps, macroscopic output to host); median of 3",
+           "runs": []}
+    for desc, ratio, eta, alpha, paper_ms in cases:
+        w = W.riemann_tube(800, ratio, 2.0, eta_over_s=eta)
+        host = [np.ascontiguousarray(a) for a in w.fields()]
+        outbuf = np.empty((6, w.N))
+        res = {"workload": desc, "steps": 1600, "paper_ms": paper_ms,
+               "paper_hardware": "an unnamed 'standard PC' CPU (core count and precision not stated)"}
+        for key, prec, sym in (("fp64_ms", rlb.FP64, 0), ("fp32_ms", rlb.FP32_STORAGE, 0),
+                               ("fp32_symmetry_1d_ms", rlb.FP32_STORAGE, 1)):
+            g = rlb.Grid(w.nx, bc_lo=w.bc_lo, bc_hi=w.bc_hi, eta_over_s=eta, dt_over_dx=0.25,
+                         alpha_override=alpha, precision=prec, symmetry_1d=sym)
+            g.init(*host).step(10)
+            times = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g.init(*host)
+                g.step(1600)
+                rlb.rlb_macroscopic(g.ctx, outbuf, 0)
+                torch.cuda.synchronize()
+                times.append(1e3 * (time.perf_counter() - t0))
+            g.close()
+            res[key] = sorted(times)[1]
+        p = oracle.Params(nx=800, dt=0.25, eta_over_s=eta, alpha_override=alpha)
+        t0 = time.perf_counter()
+        st = oracle.init(p, *host)
+        oracle.step(st, 1600)
+        oracle.macroscopic(st)
+        res["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
+        res["oracle_cores"] = oracle.get_threads()
+        res["oracle_nonphysical_cells"] = int(st.nonphysical)
+        out["runs"].append(res)
+    return out
+
+
 def basic_model_run(torch, rlb, W, hbm_peak):
     """The basic model (Sec. II: D3Q19 with unit diagonals) on the headline
     grid, and the paper's basic-versus-extended comparison (P ratio 32,
@@ -569,6 +618,7 @@ def run_ours(args):
     batch = batch_sweep(torch, rlb, W, hbm_peak, local) if not args.no_batch else None
     sphere = sphere_run(torch, rlb, W, local) if not args.no_batch else None
     cloud2d = cloud_2d_run(torch, rlb, W, hbm_peak) if not args.no_batch else None
+    paper = paper_runs(torch, rlb, W) if not args.no_batch and (world == 1 or rank == 0) else None
     basic = basic_model_run(torch, rlb, W, hbm_peak) if not args.no_batch else None
     if rank != 0:
         return 0
@@ -601,6 +651,7 @@ def run_ours(args):
         "batch": batch,
         "sphere_cloud": sphere,
         "cloud_2d": cloud2d,
+        "paper_runs": paper,
         "basic_model": basic,
     }
     print(json.dumps(line), flush=True)
