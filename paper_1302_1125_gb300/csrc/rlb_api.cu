@@ -40,7 +40,7 @@ struct rlb_ctx {
     cudaStream_t stream;
     long long launches;
     StepParams sp;
-    bool sym_stale = false;   // 2-D symmetry reduction: mirror-image planes not yet refreshed
+    bool sym_stale = false;   // symmetry reduction: the non-representative class planes are not yet refreshed
     std::string err;
 };
 
@@ -394,6 +394,7 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
     if (!ctx) return fail(nullptr, RLB_E_INVALID, "ctx is NULL");
     if (nsteps < 0) return fail(ctx, RLB_E_INVALID, "nsteps must be >= 0");
     RLB_CUDA(ctx, cudaSetDevice(ctx->device));
+    if (nsteps > 0 && ctx->sp.sym) ctx->sym_stale = true;   // set first: a failed launch may follow steps that ran
     for (long long k = 0; k < nsteps; ++k) {
         const int c = ctx->cur, o = 1 - c;
         cudaError_t e;
@@ -415,7 +416,6 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
             ctx->launches += 1;
         }
     }
-    if (nsteps > 0 && ctx->sp.sym) ctx->sym_stale = true;
     return check_device_status(ctx, RLB_E_NONPHYSICAL);
 }
 
