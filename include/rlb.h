@@ -94,7 +94,7 @@ typedef struct {
     int precision;           /* RLB_FP64 or RLB_FP32_STORAGE */
     void *cuda_stream;       /* cudaStream_t, NULL = legacy default stream */
     int symmetry_1d;         /* 1: exact 1-D symmetry reduction, for batched tubes and for
-                              * FP32-storage grids with ny = nz = 1 (viscous step).  With
+                              * grids with ny = nz = 1 (either precision, viscous step).  With
                               * u_y = u_z = 0 and fields uniform in y and z, populations with
                               * the same weight and the same c_x stay equal, leaving 7 classes
                               * per distribution (rest, +x, -x, the y/z axis populations, the
@@ -119,7 +119,7 @@ typedef struct {
                               * run of consecutive cells (pairs) of the x-fastest order, no idle
                               * lanes whatever nx and ny.  The results are the same bit for
                               * bit. */
-    int symmetry_2d;         /* 1 (FP32-storage grids with nz = 1 < ny, viscous step): exact 2-D
+    int symmetry_2d;         /* 1 (grids with nz = 1 < ny, either precision, viscous step): exact 2-D
                               * symmetry reduction.  With u_z = 0 in every cell (and at the
                               * inlet) the state is its own mirror image in z, so mirror-image
                               * populations stay equal: 14 classes per distribution (rest, +x,

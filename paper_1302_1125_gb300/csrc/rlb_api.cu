@@ -127,8 +127,7 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.euler_mode != 0 && o.euler_mode != 1) return fail(ctx, RLB_E_INVALID, "euler_mode must be 0 or 1");
     if (o.symmetry_1d != 0 && o.symmetry_1d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_1d must be 0 or 1");
     if (o.symmetry_1d) {
-        if (o.precision != RLB_FP32_STORAGE || o.euler_mode != 0)
-            return fail(ctx, RLB_E_INVALID, "symmetry_1d needs the FP32-storage form and the viscous step");
+        if (o.euler_mode != 0) return fail(ctx, RLB_E_INVALID, "symmetry_1d needs the viscous step");
         if (g.ny != 1 || g.nz != 1)
             return fail(ctx, RLB_E_INVALID, "symmetry_1d on a grid needs a 1-D grid (ny = nz = 1)");
         if ((g.bc_lo[0] == RLB_BC_INLET || g.bc_hi[0] == RLB_BC_INLET) && (g.inlet_u[1] != 0.0 || g.inlet_u[2] != 0.0))
@@ -140,8 +139,7 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
     if (o.symmetry_2d != 0 && o.symmetry_2d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_2d must be 0 or 1");
     if (o.symmetry_1d && o.symmetry_2d) return fail(ctx, RLB_E_INVALID, "symmetry_1d and symmetry_2d exclude each other");
     if (o.symmetry_2d) {
-        if (o.precision != RLB_FP32_STORAGE || o.euler_mode != 0)
-            return fail(ctx, RLB_E_INVALID, "symmetry_2d needs the FP32-storage form and the viscous step");
+        if (o.euler_mode != 0) return fail(ctx, RLB_E_INVALID, "symmetry_2d needs the viscous step");
         if (g.nz != 1 || g.ny < 2)
             return fail(ctx, RLB_E_INVALID, "symmetry_2d needs a 2-D grid (nz = 1 < ny)");
         if ((g.bc_lo[0] == RLB_BC_INLET || g.bc_hi[0] == RLB_BC_INLET) && g.inlet_u[2] != 0.0)
@@ -210,8 +208,8 @@ rlb_status check_device_status(rlb_ctx *ctx, rlb_status if_bad)
 rlb_status refresh_mirrors(rlb_ctx *ctx)
 {
     if (!ctx->sp.sym || !ctx->sym_stale) return RLB_OK;
-    RLB_CUDA(ctx, rlb::launch_sym(1, ctx->sp.sym, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur],
-                                  (float *)ctx->hbuf[ctx->cur], (float *)ctx->prev, ctx->d_status, ctx->stream));
+    RLB_CUDA(ctx, rlb::launch_sym(ctx->fp32, 1, ctx->sp.sym, ctx->N, ctx->ps, ctx->fbuf[ctx->cur],
+                                  ctx->hbuf[ctx->cur], ctx->prev, ctx->d_status, ctx->stream));
     ctx->launches += 1;
     ctx->sym_stale = false;
     return RLB_OK;
@@ -524,9 +522,8 @@ static rlb_status copy_state(rlb_ctx *ctx, void *buf, size_t bytes, bool out)
         // a reduction steps the class representatives only: every member of
         // a class must equal its representative
         ctx->sym_stale = false;
-        RLB_CUDA(ctx, rlb::launch_sym(0, ctx->sp.sym, ctx->N, ctx->ps, (float *)ctx->fbuf[ctx->cur],
-                                      (float *)ctx->hbuf[ctx->cur], (float *)ctx->prev, ctx->d_status,
-                                      ctx->stream));
+        RLB_CUDA(ctx, rlb::launch_sym(ctx->fp32, 0, ctx->sp.sym, ctx->N, ctx->ps, ctx->fbuf[ctx->cur],
+                                      ctx->hbuf[ctx->cur], ctx->prev, ctx->d_status, ctx->stream));
         ctx->launches += 1;
         return check_device_status(ctx, RLB_E_INVALID);
     }

@@ -6,15 +6,18 @@
 
 namespace rlb {
 
+// (sym: the state must have u_y = u_z = 0 for the 1-D symmetry reduction,
+// u_z = 0 for the 2-D one)
 template <typename T, int LAT>
 __global__ void init_kernel(int N, long long ps, const double *__restrict__ n,
                             const double *__restrict__ Tt, const double *__restrict__ ux,
                             const double *__restrict__ uy, const double *__restrict__ uz,
                             T *__restrict__ f, T *__restrict__ h, T *__restrict__ prev,
-                            unsigned *status)
+                            unsigned *status, int sym)
 {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= N) return;
+    if (sym && (uz[idx] != 0.0 || (sym == 1 && uy[idx] != 0.0))) atomicOr(status, unsigned(ST_ASYMMETRIC));
     init_cell<T, LAT>(idx, idx, ps, n, Tt, ux, uy, uz, f, h, prev, status);
 }
 
@@ -68,8 +71,9 @@ __constant__ int kMember[2][12][2] = {
     {{3, 4}, {3, 5}, {3, 6}, {7, 8}, {7, 11}, {7, 12}, {9, 10}, {9, 13}, {9, 14}, {15, 16}, {15, 17}, {15, 18}},
     {{5, 6}, {11, 12}, {13, 14}, {15, 16}, {17, 18}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}, {0, 0}}};
 
-__global__ void sym_kernel(int expand, int sym, int N, long long ps, float *__restrict__ f, float *__restrict__ h,
-                           float *__restrict__ prev, unsigned *status)
+template <typename T>
+__global__ void sym_kernel(int expand, int sym, int N, long long ps, T *__restrict__ f, T *__restrict__ h,
+                           T *__restrict__ prev, unsigned *status)
 {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= N) return;
@@ -84,9 +88,11 @@ __global__ void sym_kernel(int expand, int sym, int N, long long ps, float *__re
             same = same && f[b] == f[a] && h[b] == h[a];
         }
     }
+    // the FP32-storage form's previous level holds raw sums (sum c_y f and
+    // sum c_z f vanish); the FP64 form's holds u' (u'_y and u'_z are zero)
     if (expand) {
-        if (sym == 1) prev[2 * ps + i] = 0.0f;
-        prev[3 * ps + i] = 0.0f;
+        if (sym == 1) prev[2 * ps + i] = T(0);
+        prev[3 * ps + i] = T(0);
     } else if (!same) {
         atomicOr(status, unsigned(ST_ASYMMETRIC));
     }
@@ -165,12 +171,15 @@ __global__ void totals_finish(int nblocks, const double *__restrict__ partial, d
 }
 
 
-cudaError_t launch_sym(int expand, int sym, int N, long long ps, float *f, float *h, float *prev,
+cudaError_t launch_sym(int fp32, int expand, int sym, int N, long long ps, void *f, void *h, void *prev,
                        unsigned *status, cudaStream_t s)
 {
     if (sym != 1 && sym != 2) return cudaErrorInvalidValue;
     const int b = 256, g = (N + b - 1) / b;
-    sym_kernel<<<g, b, 0, s>>>(expand, sym, N, ps, f, h, prev, status);
+    if (fp32)
+        sym_kernel<float><<<g, b, 0, s>>>(expand, sym, N, ps, (float *)f, (float *)h, (float *)prev, status);
+    else
+        sym_kernel<double><<<g, b, 0, s>>>(expand, sym, N, ps, (double *)f, (double *)h, (double *)prev, status);
     return cudaGetLastError();
 }
 
@@ -186,7 +195,7 @@ cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const do
                                                 status, sym);
         else
             init_kernel<double, L><<<g, b, 0, s>>>(N, ps, n, T, ux, uy, uz, (double *)f, (double *)h,
-                                                   (double *)prev, status);
+                                                   (double *)prev, status, sym);
     };
     if (lat == 1) go(std::integral_constant<int, 1>{});
     else go(std::integral_constant<int, 0>{});

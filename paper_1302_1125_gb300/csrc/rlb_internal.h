@@ -21,7 +21,7 @@ struct StepParams {
     unsigned *status;        // device status word (bit 0: non-physical cell)
     int lat;                 // lattice: 0 extended (Sec. II.A), 1 basic (Sec. II)
     int mapping;             // grids: 0 automatic, 1 tiles, 2 linear (rlb_options.thread_mapping)
-    int sym;                 // FP32 grids: exact symmetry reduction, 1 on 1-D grids (7 planes per
+    int sym;                 // grids: exact symmetry reduction, 1 on 1-D grids (7 planes per
                              // distribution), 2 on 2-D grids (14 planes: mirror images in z), 0 none
     // float copies for the FP32-storage kernel (no FP64 conversion on device)
     float f_k1, f_k2, f_half_lim, f_kw, f_kbulk, f_eta_over_s, f_tau_override;
@@ -39,12 +39,12 @@ cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float
 cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const double *T,
                         const double *ux, const double *uy, const double *uz, void *f, void *h,
                         void *prev, unsigned *status, cudaStream_t s, int lat = 0, int sym = 0);
-// symmetry reductions of FP32 grids (sym = 1: 1-D, 2: 2-D): expand = 1
-// copies each class representative's plane into its members' and zeroes the
-// previous level's sums that vanish (c_y f and c_z f, or c_z f); expand = 0
-// sets ST_ASYMMETRIC in *status where a member differs from its
-// representative
-cudaError_t launch_sym(int expand, int sym, int N, long long ps, float *f, float *h, float *prev,
+// symmetry reductions of grids (sym = 1: 1-D, 2: 2-D; float or double
+// planes per fp32): expand = 1 copies each class representative's plane into
+// its members' and zeroes the previous level's entries that vanish (the y and
+// z, or the z, components); expand = 0 sets ST_ASYMMETRIC in *status where a
+// member differs from its representative
+cudaError_t launch_sym(int fp32, int expand, int sym, int N, long long ps, void *f, void *h, void *prev,
                        unsigned *status, cudaStream_t s);
 cudaError_t launch_macro(int fp32, int N, long long ps, const void *f, const void *h, double *out,
                          unsigned *status, cudaStream_t s, int lat = 0);

@@ -11,6 +11,7 @@
 
 #include <utility>
 
+#include "rlb_classes.cuh"
 #include "rlb_device.cuh"
 #include "rlb_internal.h"
 
@@ -101,7 +102,9 @@ __device__ __forceinline__ void flag(const StepParams &p, unsigned bits)
 // order (grids whose nx, ny do not fill the tiles); otherwise blocks of
 // 32 x 4 threads take tiles of 32 x 4 cells in one z-plane (the 1-D form:
 // one row of tiles)
-template <typename T, int DIM, bool EULER, int LAT, bool LIN = false>
+// NP = 7 or 14: the 1-D or 2-D symmetry reduction (rlb_classes.cuh); only
+// the class representatives' planes are read and written
+template <typename T, int DIM, bool EULER, int LAT, bool LIN = false, int NP = 19>
 __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *__restrict__ f,
                                                    const T *__restrict__ h, T *__restrict__ fo,
                                                    T *__restrict__ ho, T *__restrict__ prev)
@@ -130,20 +133,24 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
 
     const T k1 = T(p.k1), k2 = T(p.k2), hl = T(p.half_lim), kbulk = T(p.kbulk);
 
+    static_assert(NP == 19 || (NP == 7 && DIM == 1 && !EULER) || (NP == 14 && DIM == 2 && !EULER),
+                  "the symmetry reductions are 1-D or 2-D and viscous");
     if constexpr (!EULER) {
-        // moments of f(t), h(t) at the cell (Eq. 36 with p_i^0 = xi0)
-        T fl[19], hq[19];
+        // moments of f(t), h(t) at the cell (Eq. 36 with p_i^0 = xi0); class k
+        // counts mult(k) equal populations (powers of two: exact scaling)
+        T fl[NP], hq[NP];
         double sf = 0.0, sh = 0.0, mx = 0.0, my = 0.0, mz = 0.0;
-        for_pops(RLB_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            fl[I] = ldg(f + I * ps + idx);
-            hq[I] = ldg(h + I * ps + idx);
-            const double fv = double(fl[I]);
-            sf += fv;
-            sh += double(hq[I]);
-            if constexpr (cdir<I, 0, LAT>() != 0) mx += double(cdir<I, 0, LAT>()) * fv;
-            if constexpr (cdir<I, 1, LAT>() != 0) my += double(cdir<I, 1, LAT>()) * fv;
-            if constexpr (cdir<I, 2, LAT>() != 0) mz += double(cdir<I, 2, LAT>()) * fv;
+        for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int I = rep<NP>(k), m = mult<NP>(k);
+            fl[k] = ldg(f + I * ps + idx);
+            hq[k] = ldg(h + I * ps + idx);
+            const double fv = double(fl[k]);
+            sf += m == 1 ? fv : double(m) * fv;
+            sh += m == 1 ? double(hq[k]) : double(m) * double(hq[k]);
+            if constexpr (cdir<I, 0, LAT>() != 0) mx += double(cdir<I, 0, LAT>() * m) * fv;
+            if constexpr (has_vy<NP>() && cdir<I, 1, LAT>() != 0) my += double(cdir<I, 1, LAT>() * m) * fv;
+            if constexpr (has_vz<NP>() && cdir<I, 2, LAT>() != 0) mz += double(cdir<I, 2, LAT>() * m) * fv;
         });
         Macro mt;
         const bool ok = recover(Lat<LAT>::xi0sq * sf, Lat<LAT>::xi0 * mx, Lat<LAT>::xi0 * my, Lat<LAT>::xi0 * mz, Lat<LAT>::xi0 * sh, mt);
@@ -169,15 +176,17 @@ __global__ void __launch_bounds__(128) step_kernel(const StepParams p, const T *
         coef_h<LAT>(mp, b);
         const EqW<T> kh = weigh_h<T, LAT>(extrapolate(a, b));
 
-        for_pops(RLB_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            const T pre = streamed<T, DIM, true, I, LAT>(f + I * ps, idx, am, fl[I], T(p.ghost_f[I]), k1,
+        for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int I = rep<NP>(k);
+            const T pre = streamed<T, DIM, true, I, LAT>(f + I * ps, idx, am, fl[k], T(p.ghost_f[I]), k1,
                                                     k2, hl, kbulk);
             fo[I * ps + idx] = pre + kap * (eq_pop<I>(kf) - pre);
         });
-        for_pops(RLB_POPS, [&](auto ic) {
-            constexpr int I = decltype(ic)::value;
-            const T pre = streamed<T, DIM, false, I, LAT>(h + I * ps, idx, am, hq[I], T(p.ghost_h[I]),
+        for_pops(std::make_integer_sequence<int, NP>{}, [&](auto kc) {
+            constexpr int k = decltype(kc)::value;
+            constexpr int I = rep<NP>(k);
+            const T pre = streamed<T, DIM, false, I, LAT>(h + I * ps, idx, am, hq[k], T(p.ghost_h[I]),
                                                      k1, k2, hl, kbulk);
             ho[I * ps + idx] = pre + kap * (eq_pop<I>(kh) - pre);
         });

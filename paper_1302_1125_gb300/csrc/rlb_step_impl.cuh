@@ -20,8 +20,8 @@ inline int sm_count()
     return n;
 }
 
-template <typename T, int DIM, bool EULER, int LAT>
-cudaError_t launch_step_t(const StepParams &p, const T *f, const T *h, T *fo, T *ho, T *prev,
+template <typename T, int DIM, bool EULER, int LAT, int NP>
+cudaError_t launch_step_np(const StepParams &p, const T *f, const T *h, T *fo, T *ho, T *prev,
                           cudaStream_t s)
 {
     const long long cells = (long long)p.nx * p.ny * p.nz;
@@ -35,25 +35,40 @@ cudaError_t launch_step_t(const StepParams &p, const T *f, const T *h, T *fo, T 
         int bs = int(((cells + nsm - 1) / nsm + 31) / 32 * 32);
         bs = bs < 32 ? 32 : (bs > 128 ? 128 : bs);
         const unsigned nb = unsigned((cells + bs - 1) / bs);
-        if (DIM == 1) step_kernel<T, DIM, EULER, LAT, false><<<nb, bs, 0, s>>>(p, f, h, fo, ho, prev);
-        else step_kernel<T, DIM, EULER, LAT, true><<<nb, bs, 0, s>>>(p, f, h, fo, ho, prev);
+        if constexpr (DIM == 1) step_kernel<T, DIM, EULER, LAT, false, NP><<<nb, bs, 0, s>>>(p, f, h, fo, ho, prev);
+        else step_kernel<T, DIM, EULER, LAT, true, NP><<<nb, bs, 0, s>>>(p, f, h, fo, ho, prev);
         return cudaGetLastError();
     }
-    if (DIM == 1) {
-        step_kernel<T, DIM, EULER, LAT><<<(p.nx + 127) / 128, 128, 0, s>>>(p, f, h, fo, ho, prev);
-        return cudaGetLastError();
-    }
-    // tiles of 32 x 4 cells when nx and ny fill them, else 128 consecutive
-    // cells of the x-fastest order per block
-    const long long tiles_x = (p.nx + 31) / 32, tiles_y = (p.ny + 3) / 4;
-    const double fill = double(p.nx) * p.ny / double(tiles_x * 32 * tiles_y * 4);
-    if (p.mapping == 2 || (p.mapping == 0 && fill < 0.97)) {
-        step_kernel<T, DIM, EULER, LAT, true><<<unsigned((cells + 127) / 128), 128, 0, s>>>(p, f, h, fo, ho, prev);
+    if constexpr (DIM == 1) {
+        step_kernel<T, DIM, EULER, LAT, false, NP><<<(p.nx + 127) / 128, 128, 0, s>>>(p, f, h, fo, ho, prev);
     } else {
-        const dim3 grid(unsigned(tiles_x), unsigned(tiles_y), p.nz);
-        step_kernel<T, DIM, EULER, LAT, false><<<grid, dim3(32, 4, 1), 0, s>>>(p, f, h, fo, ho, prev);
+        // tiles of 32 x 4 cells when nx and ny fill them, else 128 consecutive
+        // cells of the x-fastest order per block
+        const long long tiles_x = (p.nx + 31) / 32, tiles_y = (p.ny + 3) / 4;
+        const double fill = double(p.nx) * p.ny / double(tiles_x * 32 * tiles_y * 4);
+        if (p.mapping == 2 || (p.mapping == 0 && fill < 0.97)) {
+            step_kernel<T, DIM, EULER, LAT, true, NP><<<unsigned((cells + 127) / 128), 128, 0, s>>>(p, f, h, fo, ho,
+                                                                                                    prev);
+        } else {
+            const dim3 grid(unsigned(tiles_x), unsigned(tiles_y), p.nz);
+            step_kernel<T, DIM, EULER, LAT, false, NP><<<grid, dim3(32, 4, 1), 0, s>>>(p, f, h, fo, ho, prev);
+        }
     }
     return cudaGetLastError();
+}
+
+// the symmetry reductions (p.sym: 1 on 1-D grids, 2 on 2-D grids; viscous)
+template <typename T, int DIM, bool EULER, int LAT>
+cudaError_t launch_step_t(const StepParams &p, const T *f, const T *h, T *fo, T *ho, T *prev,
+                          cudaStream_t s)
+{
+    if constexpr (DIM == 1 && !EULER) {
+        if (p.sym == 1) return launch_step_np<T, 1, false, LAT, 7>(p, f, h, fo, ho, prev, s);
+    }
+    if constexpr (DIM == 2 && !EULER) {
+        if (p.sym == 2) return launch_step_np<T, 2, false, LAT, 14>(p, f, h, fo, ho, prev, s);
+    }
+    return launch_step_np<T, DIM, EULER, LAT, 19>(p, f, h, fo, ho, prev, s);
 }
 
 template <typename T, int LAT>

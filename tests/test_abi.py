@@ -78,7 +78,7 @@ def cfg(**kw):
     ({"alpha_override": 1.0}, rlb.RLB_E_UNSTABLE),       # 2 (c0 nu/ct) dt alpha > 1
     ({"alpha_override": 0.5}, rlb.RLB_OK),
     ({"dt_over_dx": -1.0}, rlb.RLB_E_INVALID),
-    ({"symmetry_1d": 1}, rlb.RLB_E_INVALID),     # FP32 storage only
+    ({"symmetry_1d": 1}, rlb.RLB_OK),            # a 1-D grid, FP64
     ({"symmetry_1d": 1, "precision": 1}, rlb.RLB_OK),
     ({"symmetry_1d": 1, "precision": 1, "ny": 8}, rlb.RLB_E_INVALID),     # 1-D grids only
     ({"symmetry_1d": 1, "precision": 1, "euler_mode": 1}, rlb.RLB_E_INVALID),
@@ -91,7 +91,7 @@ def cfg(**kw):
     ({"thread_mapping": 2, "ny": 8, "nz": 8}, rlb.RLB_OK),
     ({"symmetry_2d": 1, "ny": 8, "precision": 1}, rlb.RLB_OK),
     ({"symmetry_2d": 2, "ny": 8, "precision": 1}, rlb.RLB_E_INVALID),
-    ({"symmetry_2d": 1, "ny": 8}, rlb.RLB_E_INVALID),                       # FP32 storage only
+    ({"symmetry_2d": 1, "ny": 8}, rlb.RLB_OK),                              # FP64 too
     ({"symmetry_2d": 1, "ny": 8, "precision": 1, "euler_mode": 1}, rlb.RLB_E_INVALID),
     ({"symmetry_2d": 1, "precision": 1}, rlb.RLB_E_INVALID),                # 1-D grid
     ({"symmetry_2d": 1, "ny": 8, "nz": 4, "precision": 1}, rlb.RLB_E_INVALID),   # 3-D grid

@@ -1,7 +1,7 @@
-"""The exact 1-D symmetry reduction on FP32-storage grids
-(rlb_options.symmetry_1d with ny = nz = 1): with u_y = u_z = 0 the step keeps
-one plane per class of equal populations (7 per distribution), as the
-batched tubes do.
+"""The exact 1-D symmetry reduction on grids (rlb_options.symmetry_1d with
+ny = nz = 1), FP32 storage and FP64: with u_y = u_z = 0 the step keeps one
+plane per class of equal populations (7 per distribution), as the batched
+tubes do.
 
 * Against the FP64 oracle: the FP32 L1 bound (1e-4) on the shock tubes of
   the benchmark's 1-D configurations and on an odd-length tube.
@@ -11,6 +11,7 @@ batched tubes do.
   read back every class member equals its representative.
 * rlb_init rejects u_y or u_z != 0; rlb_set_state rejects unequal class
   members and resumes a symmetric state bit for bit.
+* The FP64 form under the reduction meets the 1e-10 bar against the oracle.
 """
 import numpy as np
 import pytest
@@ -135,3 +136,41 @@ def test_set_state_checks_the_classes():
         assert np.array_equal(a, b)
     g.close()
     g2.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_reduced_tube_matches_oracle(orc, name):
+    """the FP64 form under the reduction: the 1e-10 bar against the oracle"""
+    make, steps = CASES[name]
+    w = make()
+    g = rlb.Grid.from_workload(w, precision=rlb.FP64, symmetry_1d=1)
+    g.init(*w.fields()).step(steps)
+    mg = g.macroscopic(device=False)
+    f, h, prev = g.get_state()
+    g.close()
+    p = orc.Params(nx=w.nx, ny=w.ny, nz=w.nz, bc_lo=w.bc_lo, bc_hi=w.bc_hi, dt=w.dt_over_dx,
+                   eta_over_s=w.eta_over_s, zeta_over_s=w.zeta_over_s, tau_override=w.tau_override,
+                   alpha_override=w.alpha_override)
+    s = orc.init(p, *w.fields())
+    orc.step(s, steps)
+    mo = orc.macroscopic(s)
+    for k in (0, 1, 5):
+        assert np.abs(mg[k] - mo[k]).max() <= 1e-10 * np.abs(mo[k]).max(), k
+    assert np.abs(mg[2] - mo[2]).max() <= 1e-10 * np.abs(mo[2]).max()
+    assert np.abs(mg[3:5]).max() == 0.0
+    for a, b in MEMBERS:
+        assert np.array_equal(f[a], f[b]) and np.array_equal(h[a], h[b]), (a, b)
+    assert np.all(prev[2] == 0.0) and np.all(prev[3] == 0.0)
+
+
+def test_fp64_set_state_checks_the_classes():
+    w = W.tube_800()
+    g = rlb.Grid.from_workload(w, precision=rlb.FP64, symmetry_1d=1).init(*w.fields()).step(5)
+    f, h, prev = (a.copy() for a in g.get_state())
+    bad = f.copy()
+    bad[11, 100] *= 1.0 + 1e-12
+    with pytest.raises(rlb.RLBError) as e:
+        g.set_state(bad, h, prev)
+    assert e.value.status == rlb.RLB_E_INVALID
+    g.set_state(f, h, prev).step(2)
+    g.close()

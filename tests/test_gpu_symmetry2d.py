@@ -1,5 +1,5 @@
-"""The exact 2-D symmetry reduction of the FP32-storage grid step
-(rlb_options.symmetry_2d): on a grid with nz = 1 and u_z = 0 the state is its
+"""The exact 2-D symmetry reduction of the grid step (rlb_options.symmetry_2d),
+FP32 storage and FP64: on a grid with nz = 1 and u_z = 0 the state is its
 own mirror image in z, so the step keeps one plane per class of mirror-image
 populations (14 per distribution).
 
@@ -11,6 +11,7 @@ populations (14 per distribution).
 * Odd nx (no aligned pairs), both thread mappings, solid cells.
 * rlb_init rejects u_z != 0; rlb_set_state rejects a state whose mirror images
   differ and takes a symmetric one.
+* The FP64 form under the reduction meets the 1e-10 bar against the oracle.
 """
 import numpy as np
 import pytest
@@ -178,3 +179,24 @@ def test_full_size_cloud_2d_reduced_equals_full():
     assert np.abs(mr[4]).max() == 0.0
     full.close()
     red.close()
+
+
+@pytest.mark.parametrize("name", sorted(CASES))
+def test_fp64_reduced_step_matches_oracle(orc, name):
+    """the FP64 form under the reduction: the 1e-10 bar against the oracle"""
+    make, steps = CASES[name]
+    w = make()
+    g = rlb.Grid.from_workload(w, precision=rlb.FP64, symmetry_2d=1)
+    g.init(*[torch.as_tensor(a, device="cuda") for a in w.fields()]).step(steps)
+    mg = g.macroscopic(device=False)
+    f, h, prev = g.get_state()
+    g.close()
+    mo = oracle_macro(orc, w, steps)
+    for k in (0, 1, 5):
+        assert np.abs(mg[k] - mo[k]).max() <= 1e-10 * np.abs(mo[k]).max(), k
+    for k in (2, 3):
+        assert np.abs(mg[k] - mo[k]).max() <= 1e-10 * np.abs(mo[2:4]).max(), k
+    assert np.abs(mg[4]).max() == 0.0
+    for a, b in MIRRORS:
+        assert np.array_equal(f[a], f[b]) and np.array_equal(h[a], h[b]), (a, b)
+    assert np.all(prev[3] == 0.0)
