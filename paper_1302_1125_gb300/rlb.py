@@ -270,7 +270,17 @@ def rlb_destroy(ctx):
 
 
 class Grid:
-    """One simulation context: a grid, its populations and parameters."""
+    """One simulation context: a grid, its populations and parameters.
+
+    The keyword arguments are the fields of rlb_grid and rlb_options
+    (include/rlb.h): boundaries per face (bc_lo, bc_hi; the inlet state for
+    RLB_BC_INLET faces), eta/s and zeta/s, the limiter, dt/dx, the tau and
+    alpha overrides, Euler mode, the precision (FP64 or FP32_STORAGE), the
+    lattice (model), the CUDA stream ("current": torch's current stream),
+    the thread mapping of the grid kernels (MAPPING_AUTO, MAPPING_TILES,
+    MAPPING_LINEAR; the results are the same) and the exact symmetry
+    reductions (symmetry_1d on grids with ny = nz = 1, symmetry_2d on grids
+    with nz = 1; viscous step)."""
 
     def __init__(self, nx, ny=1, nz=1, *, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
                  bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
