@@ -35,9 +35,10 @@
  *
  * Errors.  No function throws or aborts.  Each returns an rlb_status; the
  * text of the last error of a context is available from rlb_last_error.
- * Device-side problems (a non-physical state, E <= |M| or non-finite) are
- * recorded in a device status word and reported by the next call that
- * synchronises (rlb_step, rlb_macroscopic).
+ * Device-side problems (a non-physical state, E <= |M| or non-finite; under
+ * a symmetry reduction, a state that is not symmetric) are recorded in a
+ * device status word and reported by the next call that synchronises
+ * (rlb_init, rlb_step, rlb_macroscopic, rlb_set_state).
  *
  * Streams.  All work of a context is issued on the CUDA stream given in
  * rlb_options.cuda_stream (NULL = the legacy default stream).
@@ -195,7 +196,9 @@ RLB_API rlb_status rlb_set_solid(rlb_ctx *ctx, const unsigned char *mask, double
 
 /* Macroscopic fields of the current populations (Sec. II: moments and the
  * Landau-frame recovery): out holds 6 N doubles, planes n, e, u_x, u_y, u_z,
- * gamma.  Synchronous. */
+ * gamma.  Synchronous.  Under a symmetry reduction this call, like
+ * rlb_conserved_totals and rlb_get_state, first refreshes the planes the
+ * step leaves to the class representatives (one launch, once after steps). */
 RLB_API rlb_status rlb_macroscopic(rlb_ctx *ctx, double *out, int on_device);
 
 /* Grid totals of T^00, T^0x, T^0y, T^0z and N^0 (sums over cells of the
@@ -214,7 +217,10 @@ RLB_API rlb_status rlb_conserved_totals(rlb_ctx *ctx, double *out);
 RLB_API size_t rlb_state_bytes(const rlb_ctx *ctx);
 
 /* Copy the full state out / in (checkpoint and resume).  bytes must equal
- * rlb_state_bytes.  A resumed run continues bit for bit.  Synchronous. */
+ * rlb_state_bytes.  A resumed run continues bit for bit.  Synchronous.
+ * Under a symmetry reduction rlb_set_state returns RLB_E_INVALID when a
+ * population differs from its class representative (the state must be
+ * symmetric; it is copied in all the same). */
 RLB_API rlb_status rlb_get_state(rlb_ctx *ctx, void *buf, size_t bytes, int on_device);
 RLB_API rlb_status rlb_set_state(rlb_ctx *ctx, const void *buf, size_t bytes, int on_device);
 
