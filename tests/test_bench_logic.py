@@ -1,0 +1,78 @@
+"""Host logic of bench.py that decides what the bench line reports.
+
+* The clock summary parses nvidia-smi's CSV samples (median SM clock, the
+  throttle reasons seen active), and a run is rejected on a hardware or
+  thermal slowdown or on clocks stuck low with no reason; a power-cap
+  reason alone is kept.
+* The roofline's DRAM traffic comes from a committed profile summary only
+  while the hash of the profiled sources matches: any edit to those sources
+  makes it null.
+"""
+import os
+
+import pytest
+
+import bench
+
+Q = "0, {sm}, 2070, 900.5, 0x0, {hw}, {hwt}, {swt}, {pc}"
+
+
+def sampler(lines):
+    cs = bench.ClockSampler(0)
+    cs.lines = lines
+    return cs
+
+
+def line(sm, hw="Not Active", hwt="Not Active", swt="Not Active", pc="Not Active"):
+    return Q.format(sm=sm, hw=hw, hwt=hwt, swt=swt, pc=pc)
+
+
+def test_clock_summary_and_acceptance():
+    clk = sampler([line(2070), line(2070), line(2055), "garbage"]).summary()
+    assert clk == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    assert not bench.rejected(clk)
+    assert sampler([]).summary() is None
+    assert not bench.rejected(None)
+
+
+@pytest.mark.parametrize("field,reason", [("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                                          ("swt", "sw_thermal_slowdown")])
+def test_slowdowns_are_rejected(field, reason):
+    clk = sampler([line(2070), line(1500, **{field: "Active"})]).summary()
+    assert reason in clk["reasons"]
+    assert bench.rejected(clk)
+
+
+def test_power_cap_is_kept_and_a_stuck_clock_rejected():
+    capped = sampler([line(1900, pc="Active"), line(1950, pc="Active")]).summary()
+    assert capped["reasons"] == ["sw_power_cap"]
+    assert not bench.rejected(capped)
+    stuck = sampler([line(1000), line(1005)]).summary()
+    assert stuck["reasons"] == [] and bench.rejected(stuck)
+
+
+def test_profiled_traffic_follows_the_source_hash(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_1302_1125_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "a.cu").write_text("kernel a\n")
+    (csrc / "b.cuh").write_text("header b\n")
+    (tmp_path / "profiles").mkdir()
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h = bench.csrc_hash(["b.cuh", "a.cu"])
+    assert h == bench.csrc_hash(["a.cu", "b.cuh"])          # order does not matter
+    (tmp_path / "profiles" / "k.md").write_text(
+        f"# k\n\ncsrc_sha256: {h}   (note)\ncsrc_files: a.cu b.cuh\ntraffic_bytes_per_cell: 350.5\n")
+    assert bench.profiled_traffic("k.md", 1000) == pytest.approx(350500.0)
+    (csrc / "b.cuh").write_text("header b, edited\n")
+    assert bench.profiled_traffic("k.md", 1000) is None      # stale capture: no traffic
+    assert bench.profiled_traffic("missing.md", 1000) is None
+
+
+def test_committed_profiles_name_existing_sources():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    for name in os.listdir(os.path.join(root, "profiles")):
+        text = open(os.path.join(root, "profiles", name)).read()
+        for ln in text.splitlines():
+            if ln.startswith("csrc_files:"):
+                for f in ln.split(":", 1)[1].split():
+                    assert os.path.exists(os.path.join(root, "paper_1302_1125_gb300", "csrc", f)), (name, f)
