@@ -435,22 +435,42 @@ def cloud_2d_run(torch, rlb, W, hbm_peak, steps=200):
     return out
 
 
+PAPER_TUBES = [
+    ("P ratio 5.43/2.22, T ratio 2, eta/s 0.1, alpha 0 (beta ~ 0.2)", 5.43 / 2.22, 0.1, 0.0, 220.0),
+    ("P ratio 32, T ratio 2, eta/s 0.01, alpha 0.15, extended model (beta ~ 0.7)", 32.0, 0.01, 0.15, 1069.0),
+]
+
+
+def cpu_baseline_paper_tubes(W):
+    """Part of the CPU baseline: the oracle, as it stands, on the paper's timed
+    1-D runs (the cases of PAPER_TUBES, 1600 steps each, init and
+    macroscopic output included) on all host cores."""
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
+    out = []
+    for _desc, ratio, eta, alpha, _paper_ms in PAPER_TUBES:
+        host = [np.ascontiguousarray(a) for a in W.riemann_tube(800, ratio, 2.0, eta_over_s=eta).fields()]
+        p = oracle.Params(nx=800, dt=0.25, eta_over_s=eta, alpha_override=alpha)
+        t0 = time.perf_counter()
+        st = oracle.init(p, *host)
+        oracle.step(st, 1600)
+        oracle.macroscopic(st)
+        out.append({"oracle_ms": 1e3 * (time.perf_counter() - t0), "oracle_cores": oracle.get_threads(),
+                    "oracle_nonphysical_cells": int(st.nonphysical)})
+    return out
+
+
 def paper_runs(torch, rlb, W):
     """The paper's timed 1-D runs (Sec. III: 800 cells, dt/dx 0.25, t = 3.2 fm,
     i.e. 1600 steps), each as a whole run through the public API with host
     arrays: rlb_init from host fields, the steps, rlb_macroscopic to host.
-    Next to them the oracle, as it stands, on the same run on the host cores,
-    and the paper's own wall times (an unnamed "standard PC"; context only)."""
-    import oracle
-    oracle.set_threads(os.cpu_count() or 1)
-    cases = [
-        ("P ratio 5.43/2.22, T ratio 2, eta/s 0.1, alpha 0 (beta ~ 0.2)", 5.43 / 2.22, 0.1, 0.0, 220.0),
-        ("P ratio 32, T ratio 2, eta/s 0.01, alpha 0.15, extended model (beta ~ 0.7)", 32.0, 0.01, 0.15, 1069.0),
-    ]
+    Next to them the paper's own wall times (an unnamed "standard PC";
+    context only); the oracle's times on the same runs come from
+    cpu_baseline_paper_tubes."""
     out = {"what": "the paper's timed 1-D runs: 800 cells, dt/dx 0.25, 1600 steps; wall time of the whole run "
                    "(init from host, steps, macroscopic output to host); median of 3",
            "runs": []}
-    for desc, ratio, eta, alpha, paper_ms in cases:
+    for desc, ratio, eta, alpha, paper_ms in PAPER_TUBES:
         w = W.riemann_tube(800, ratio, 2.0, eta_over_s=eta)
         host = [np.ascontiguousarray(a) for a in w.fields()]
         outbuf = np.empty((6, w.N))
@@ -472,14 +492,6 @@ def paper_runs(torch, rlb, W):
                 times.append(1e3 * (time.perf_counter() - t0))
             g.close()
             res[key] = sorted(times)[1]
-        p = oracle.Params(nx=800, dt=0.25, eta_over_s=eta, alpha_override=alpha)
-        t0 = time.perf_counter()
-        st = oracle.init(p, *host)
-        oracle.step(st, 1600)
-        oracle.macroscopic(st)
-        res["oracle_ms"] = 1e3 * (time.perf_counter() - t0)
-        res["oracle_cores"] = oracle.get_threads()
-        res["oracle_nonphysical_cells"] = int(st.nonphysical)
         out["runs"].append(res)
     return out
 
@@ -624,6 +636,9 @@ def run_ours(args):
         return 0
     l1 = l1_fp32_vs_fp64(torch)
     base = cpu_baseline()[0] if world == 1 or rank == 0 else None
+    if paper is not None:
+        for run, orc_time in zip(paper["runs"], cpu_baseline_paper_tubes(W)):
+            run.update(orc_time)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": per_step, "higher_is_better": True,

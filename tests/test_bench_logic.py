@@ -76,3 +76,40 @@ def test_committed_profiles_name_existing_sources():
             if ln.startswith("csrc_files:"):
                 for f in ln.split(":", 1)[1].split():
                     assert os.path.exists(os.path.join(root, "paper_1302_1125_gb300", "csrc", f)), (name, f)
+
+
+def _oracle_import_sites(path):
+    """(enclosing top-level function or None, line) of every import of oracle"""
+    import ast
+    tree = ast.parse(open(path).read())
+    sites = []
+    for top in tree.body:
+        name = top.name if isinstance(top, (ast.FunctionDef, ast.AsyncFunctionDef)) else None
+        for node in ast.walk(top):
+            mods = []
+            if isinstance(node, ast.Import):
+                mods = [a.name for a in node.names]
+            elif isinstance(node, ast.ImportFrom):
+                mods = [node.module or ""]
+            if any(m == "oracle" or m.startswith("oracle.") for m in mods):
+                sites.append((name, node.lineno))
+    return sites
+
+
+def test_oracle_is_used_only_by_the_baseline_legs_and_the_entry_checks():
+    """the product path never reaches the oracle: bench.py imports it only in
+    its CPU-baseline functions, __graft_entry__ only in build (which compiles
+    it) and smoke (which checks against it), the package not at all"""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sites = _oracle_import_sites(os.path.join(root, "bench.py"))
+    assert sites and all(f is not None and f.startswith("cpu_baseline") for f, _ in sites), sites
+    sites = _oracle_import_sites(os.path.join(root, "__graft_entry__.py"))
+    assert {f for f, _ in sites} <= {"build", "smoke"}, sites
+    pkg = os.path.join(root, "paper_1302_1125_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith(".py"):
+                assert not _oracle_import_sites(os.path.join(dirpath, fn)), fn
+            if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, fn)).read()
+                assert "rlb_oracle" not in text and "orc_" not in text, fn
