@@ -10,8 +10,11 @@ Eq. 55, a dropped nu in the collision prefactor of Eq. 57, the wrong sign of
 the extrapolated equilibrium, n = N^0 gamma, a flipped lattice vector, tau
 without nu^2 (Eq. 41), minmod taking the larger slope (Eq. 53), and in the
 solid cells of the astrophysical run (Sec. III): no reset, a moving or a
-wrong-pressure cloud state; and in the basic model's lattice (Sec. II): a
-mistyped weight, doubled diagonals, swapped number weights.
+wrong-pressure cloud state; in the basic model's lattice (Sec. II): a
+mistyped weight, doubled diagonals, swapped number weights; Euler mode
+(Sec. III) taking the equilibria of the unstreamed state; the bulk term of
+Eq. 57 applied to the number distribution as well; an inlet ghost whose
+pressure drops the temperature.
 """
 import os
 import subprocess
@@ -23,7 +26,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "rlb_oracle.c")
 PINS = ["tests/test_oracle_lattice.py", "tests/test_oracle_equilibrium.py",
         "tests/test_oracle_stream.py", "tests/test_oracle_step.py", "tests/test_oracle_solid.py",
-        "tests/test_oracle_basic.py"]
+        "tests/test_oracle_basic.py", "tests/test_oracle_hydro.py"]
 
 MUTATIONS = {
     "printed_delta_plus_in_fR": ("fR -= 0.5 * orc_minmod(dm_y, dm_yp1);",
@@ -54,6 +57,14 @@ MUTATIONS = {
     "solid_reset_skipped": ("if (!mask[idx]) continue;", "if (mask[idx] || !mask[idx]) continue;"),
     "solid_state_moving": ("const double rest[3] = {0.0, 0.0, 0.0};", "const double rest[3] = {0.05, 0.0, 0.0};"),
     "solid_pressure_without_T": ("orc_feq(n * T, rest, fe);", "orc_feq(n, rest, fe);"),
+    "euler_mode_without_streaming": ("            fs[i] = f[i] + sf[i];\n            hs[i] = h[i] + sh[i];",
+                                     "            fs[i] = f[i];\n            hs[i] = h[i];"),
+    "bulk_term_on_number_distribution": (
+        "sh[i] = stream_at(p, H, i, k->ghost_h[i], L->c[i], kstream, x, y, z);  /* no lambda term */",
+        "sh[i] = stream_at(p, H, i, k->ghost_h[i], L->c[i], kstream, x, y, z)"
+        " + (i != 0 ? kbulk * lap_at(p, H, i, k->ghost_h[i], x, y, z) : 0.0);"),
+    "inlet_pressure_without_T": ("orc_feq(p->inlet_n * p->inlet_T, up, k->ghost_f);",
+                                 "orc_feq(p->inlet_n, up, k->ghost_f);"),
     "minmod_takes_larger_slope": ("return 0.5 * fmin(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));",
                                   "return 0.5 * fmax(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));"),
 }
