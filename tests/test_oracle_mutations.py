@@ -14,7 +14,8 @@ wrong-pressure cloud state; in the basic model's lattice (Sec. II): a
 mistyped weight, doubled diagonals, swapped number weights; Euler mode
 (Sec. III) taking the equilibria of the unstreamed state; the bulk term of
 Eq. 57 applied to the number distribution as well; an inlet ghost whose
-pressure drops the temperature.
+pressure drops the temperature; open ends that reflect instead of copying
+the edge cell.
 """
 import os
 import subprocess
@@ -65,6 +66,8 @@ MUTATIONS = {
         " + (i != 0 ? kbulk * lap_at(p, H, i, k->ghost_h[i], x, y, z) : 0.0);"),
     "inlet_pressure_without_T": ("orc_feq(p->inlet_n * p->inlet_T, up, k->ghost_f);",
                                  "orc_feq(p->inlet_n, up, k->ghost_f);"),
+    "outflow_ghosts_reflecting": ("if (bc == ORC_BC_OUTFLOW) return c < 0 ? 0 : n - 1;",
+                                  "if (bc == ORC_BC_OUTFLOW) return c < 0 ? -c : 2 * n - 2 - c;"),
     "minmod_takes_larger_slope": ("return 0.5 * fmin(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));",
                                   "return 0.5 * fmax(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));"),
 }

@@ -135,6 +135,24 @@ def test_boundaries(orc):
                        orc.stream(p, np.roll(q, 3), [0.9, 0, 0], 0.2), atol=1e-15)
 
 
+@pytest.mark.parametrize("limiter", [0, 1])
+def test_outflow_ghosts_copy_the_edge_cell(orc, limiter):
+    """Zero-gradient open ends (Sec. III): both ghost cells past an end hold
+    the edge cell's value.  So the upstream edge cell receives its own value
+    through the open face and its increment is zero whatever the data, and
+    the Laplacian there is the one-sided difference q[1] - q[0]."""
+    nx = 12
+    q = np.random.default_rng(8).normal(size=nx)
+    p = P1(orc, nx, bc=(1, 0, 0), limiter=limiter)
+    up = orc.stream(p, q, [0.8, 0, 0], 0.3)      # moving right: x = 0 is upstream
+    down = orc.stream(p, q, [-0.8, 0, 0], 0.3)   # moving left: x = nx - 1 is upstream
+    assert up[0] == 0.0 and down[-1] == 0.0
+    assert up[-1] != 0.0 and down[0] != 0.0
+    lap = orc.laplacian(p, q)
+    assert lap[0] == pytest.approx(q[1] - q[0], abs=1e-15)
+    assert lap[-1] == pytest.approx(q[-2] - q[-1], abs=1e-15)
+
+
 def test_laplacian_closed_forms(orc):
     nx, ny, nz = 9, 8, 7
     zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
