@@ -2,6 +2,7 @@
 point include/rlb.h declares, and validates configurations on the host
 (rlb_check_config and the argument checks of rlb_create run before any CUDA
 call)."""
+import ctypes
 import math
 import os
 import re
@@ -132,3 +133,30 @@ def test_null_handles_are_rejected(lib):
     assert L.rlb_init(None, None, None, None, None, None, 0) == rlb.RLB_E_INVALID
     assert L.rlb_state_bytes(None) == 0
     L.rlb_destroy(None)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """every field of the binding's ctypes structures sits at the offset, and
+    every structure has the size, that a C compiler gives the header's"""
+    structs = {"rlb_grid": rlb.rlb_grid, "rlb_options": rlb.rlb_options,
+               "rlb_batch_tuning": rlb.rlb_batch_tuning}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rlb.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} sizeof %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)],
+                   check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for ln in filter(None, out):
+        name, field, value = ln.split()
+        cls = structs[name]
+        expect = ctypes.sizeof(cls) if field == "sizeof" else getattr(cls, field).offset
+        assert int(value) == expect, (name, field)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
