@@ -139,7 +139,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     """every field of the binding's ctypes structures sits at the offset, and
     every structure has the size, that a C compiler gives the header's"""
     structs = {"rlb_grid": rlb.rlb_grid, "rlb_options": rlb.rlb_options,
-               "rlb_batch_tuning": rlb.rlb_batch_tuning}
+               "rlb_batch_tuning": rlb.rlb_batch_tuning,
+            "rlb_ctx *": ctypes.c_void_p, "rlb_batch *": ctypes.c_void_p}   # opaque handles
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "rlb.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'    printf("{name} sizeof %zu\\n", sizeof({name}));')
@@ -160,3 +161,55 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(value) == expect, (name, field)
         seen += 1
     assert seen == sum(len(c._fields_) + 1 for c in structs.values())
+
+
+def _prototypes():
+    """{name: (return type, [parameter types])} of the header's entry points"""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    out = {}
+    for ret, name, params in re.findall(r"RLB_API\s+([^;(]*?)\s*\b(rlb_\w+)\s*\(([^)]*)\)\s*;", src, re.S):
+        ps = [" ".join(p.split()) for p in params.split(",")]
+        ps = [] if ps == ["void"] else ps
+        out[name] = (" ".join(ret.split()), ps)
+    return out
+
+
+_SCALARS = {"int": ctypes.c_int, "double": ctypes.c_double, "long long": ctypes.c_longlong,
+            "size_t": ctypes.c_size_t, "rlb_status": ctypes.c_int, "unsigned char": ctypes.c_ubyte,
+            "char": ctypes.c_char, "rlb_grid": rlb.rlb_grid, "rlb_options": rlb.rlb_options,
+            "rlb_batch_tuning": rlb.rlb_batch_tuning,
+            "rlb_ctx *": ctypes.c_void_p, "rlb_batch *": ctypes.c_void_p}   # opaque handles
+
+
+def _ctype_matches(c_decl, ct):
+    """a C declaration ("const double *out", "long long n") against a ctypes
+    type: scalars exactly; a pointer as c_void_p (opaque or untyped), or as
+    POINTER of the pointee's type"""
+    t = re.sub(r"\b(const|restrict)\b", "", c_decl).strip()
+    if not t.endswith("*"):
+        t = re.sub(r"\s*\w+$", "", t)
+    t = " ".join(t.replace("*", " * ").split())
+    if t.endswith("*"):
+        base = t[:-1].strip()
+        if ct is ctypes.c_void_p:
+            return True
+        if ct is ctypes.c_char_p:
+            return base == "char"
+        return (isinstance(ct, type) and issubclass(ct, ctypes._Pointer)
+                and _SCALARS.get(base) is ct._type_)
+    return _SCALARS.get(t) is ct
+
+
+def test_binding_signatures_match_the_header(lib):
+    protos = _prototypes()
+    assert sorted(protos) == declared()
+    for name, (ret, params) in protos.items():
+        fn = getattr(lib, name)
+        assert fn.argtypes is not None, name
+        assert len(fn.argtypes) == len(params), (name, params)
+        for decl, ct in zip(params, fn.argtypes):
+            assert _ctype_matches(decl, ct), (name, decl, ct)
+        if ret == "void":
+            assert fn.restype is None, name
+        else:
+            assert _ctype_matches(ret + " r", fn.restype), (name, ret, fn.restype)
