@@ -11,6 +11,15 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
   while f does.
 * An inlet face holding the gas's own state (Sec. III) is invisible: a
   uniform moving state next to it stays uniform.
+* Shear viscosity: the Chapman-Enskog expansion of the continuum limit of
+  Eq. 57, df_i/dt + (c0/c_t) c_i . grad f_i = -(c0 nu/(c_t tau)) (f_i - f^eq_i),
+  gives for a transverse shear wave the momentum flux
+  -(c0/c_t)^2 tau_R xi0 sum_i c_x^2 c_y df^eq_i/dx with tau_R = c_t tau/(c0 nu),
+  so with the first-order coefficient 4 P gamma/(xi0 sigma2) of f^eq the shear
+  viscosity is eta = (c0/c_t) tau 4 P m22 / (nu sigma2), sigma2 = sum w c_x^2,
+  m22 = sum w c_x^2 c_y^2: 0.2369 P tau on the extended lattice, 0.1621 P tau
+  on the basic one, with no dependence on dt.  A shear wave's decay rate
+  eta k^2/(e + P) matches it on both lattices.
 """
 import math
 
@@ -85,3 +94,41 @@ def test_inlet_at_the_gas_state_is_invisible(orc, dims, u):
     s = orc.init(p, np.full(N, n), np.full(N, T), np.full(N, u[0]), np.full(N, u[1]), np.full(N, u[2]))
     orc.step(s, 5)
     assert np.abs(s.f - f0).max() > 1e-3 * np.abs(f0).max()
+
+
+@pytest.mark.parametrize("model,tol", [(0, 0.01), (1, 0.025)])
+@pytest.mark.parametrize("tau", [1.0, 3.0])
+def test_shear_wave_decays_at_the_chapman_enskog_viscosity(orc, model, tol, tau):
+    e, c, w, wh, xi0 = orc.lattice(model)
+    sigma2 = float((w * c[:, 0] ** 2).sum())
+    m22 = float((w * c[:, 0] ** 2 * c[:, 1] ** 2).sum())
+    nu = orc.nu(model)
+    c0_ct = nu / math.sqrt(27.0)                  # Eq. 46 (c_t/c_0 = sqrt(27)/nu)
+    eta_per_Ptau = c0_ct * 4.0 * m22 / (nu * sigma2)
+    assert eta_per_Ptau == pytest.approx({0: 0.23686, 1: 0.16206}[model], abs=1e-5)
+    nx, A = 256, 1e-4
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    mode = np.sin(k * (x + 0.5))
+    T = np.ones(nx)
+    n = n_eq(T)
+    P0 = float(n[0])
+    z = np.zeros(nx)
+    etas = []
+    for dt in (0.25, 0.1):
+        p = orc.Params(nx=nx, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=dt, tau_override=tau,
+                       alpha_override=0.0, model=model)
+        s = orc.init(p, n, T, z, A * mode, z)
+        steps = int(round(nx / (dt * tau)))        # about 1 % decay
+        amp = []
+        # the first quarter lets the viscous stress build up (over ~tau_R)
+        for k_steps in (steps // 4, steps - steps // 4):
+            orc.step(s, k_steps)
+            m = orc.macroscopic(s)
+            amp.append(2.0 / nx * float((m[3] * mode).sum()))
+        rate = math.log(amp[0] / amp[1]) / ((steps - steps // 4) * dt)
+        eta = rate * 4.0 * P0 / k ** 2              # e + P = 4 P
+        assert eta / (P0 * tau) == pytest.approx(eta_per_Ptau, rel=tol), (dt, eta / (P0 * tau))
+        assert np.abs(m[2]).max() < 1e-3 * A and np.abs(m[4]).max() == 0.0
+        etas.append(eta)
+    assert etas[0] == pytest.approx(etas[1], rel=1e-3)     # no dependence on dt
