@@ -20,6 +20,10 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
   m22 = sum w c_x^2 c_y^2: 0.2369 P tau on the extended lattice, 0.1621 P tau
   on the basic one, with no dependence on dt.  A shear wave's decay rate
   eta k^2/(e + P) matches it on both lattices.
+* The lambda_i term of Eq. 55 diffuses every moving population with the
+  same coefficient per unit time, D = (c0/c_t) nu alpha dx, and the rest
+  population not at all; momentum lives on the moving populations only, so
+  it diffuses with D and a shear wave decays at (eta/(e + P) + D) k^2.
 """
 import math
 
@@ -132,3 +136,32 @@ def test_shear_wave_decays_at_the_chapman_enskog_viscosity(orc, model, tol, tau)
         assert np.abs(m[2]).max() < 1e-3 * A and np.abs(m[4]).max() == 0.0
         etas.append(eta)
     assert etas[0] == pytest.approx(etas[1], rel=1e-3)     # no dependence on dt
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("tau,alpha", [(1.0, 0.2), (2.0, 0.05)])
+def test_bulk_term_diffuses_momentum(orc, model, tau, alpha):
+    e, c, w, wh, xi0 = orc.lattice(model)
+    sigma2 = float((w * c[:, 0] ** 2).sum())
+    m22 = float((w * c[:, 0] ** 2 * c[:, 1] ** 2).sum())
+    nu = orc.nu(model)
+    c0_ct = nu / math.sqrt(27.0)
+    eta_over_w = c0_ct * 4.0 * m22 / (nu * sigma2) * tau / 4.0     # eta/(e + P), e + P = 4 P
+    D = c0_ct * nu * alpha                                          # dx = 1
+    nx, A, dt = 256, 1e-4, 0.25
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    mode = np.sin(k * (x + 0.5))
+    T = np.ones(nx)
+    z = np.zeros(nx)
+    p = orc.Params(nx=nx, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=dt, tau_override=tau,
+                   alpha_override=alpha, model=model)
+    s = orc.init(p, n_eq(T), T, z, A * mode, z)
+    steps = int(round(0.01 / ((eta_over_w + D) * k * k * dt)))      # about 1 % decay
+    amp = []
+    for k_steps in (steps // 4, steps - steps // 4):
+        orc.step(s, k_steps)
+        amp.append(2.0 / nx * float((orc.macroscopic(s)[3] * mode).sum()))
+    rate = math.log(amp[0] / amp[1]) / ((steps - steps // 4) * dt)
+    assert rate == pytest.approx((eta_over_w + D) * k * k, rel=5e-3)
+    assert D / (eta_over_w + D) > 0.5          # the lambda term dominates here
