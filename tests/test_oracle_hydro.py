@@ -24,6 +24,12 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
   same coefficient per unit time, D = (c0/c_t) nu alpha dx, and the rest
   population not at all; momentum lives on the moving populations only, so
   it diffuses with D and a shear wave decays at (eta/(e + P) + D) k^2.
+* Particle diffusion: a density wave at uniform pressure and rest leaves f
+  uniform, and the same expansion for h (first-order part
+  -tau_R (c0/c_t) c_i . grad h^eq_i, h^eq_i = w'_i n c0/c_t at rest, and
+  N^x = sum c_x h with xi0 c0/c_t = 1) gives the diffusion coefficient
+  tau_R (c0/c_t)^2 sum w' c_x^2 = tau/(3 sqrt(27)) on both lattices, with
+  no lambda_i term (Sec. II.B): the result does not depend on alpha.
 """
 import math
 
@@ -165,3 +171,40 @@ def test_bulk_term_diffuses_momentum(orc, model, tau, alpha):
     rate = math.log(amp[0] / amp[1]) / ((steps - steps // 4) * dt)
     assert rate == pytest.approx((eta_over_w + D) * k * k, rel=5e-3)
     assert D / (eta_over_w + D) > 0.5          # the lambda term dominates here
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("tau", [1.0, 2.0])
+def test_density_wave_diffuses_at_the_chapman_enskog_rate(orc, model, tau):
+    e, c, w, wh, xi0 = orc.lattice(model)
+    nu = orc.nu(model)
+    c0_ct = nu / math.sqrt(27.0)
+    assert xi0 * c0_ct == pytest.approx(1.0, rel=1e-14)
+    tau_R = tau / (c0_ct * nu)
+    kappa = tau_R * c0_ct ** 2 * float((wh * c[:, 0] ** 2).sum())
+    assert kappa == pytest.approx(tau / (3.0 * math.sqrt(27.0)), rel=1e-12)
+    nx, A, dt = 256, 1e-3, 0.25
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    mode = np.sin(k * (x + 0.5))
+    n0 = float(n_eq(1.0))
+    n = n0 * (1.0 + A * mode)
+    T = n0 / n                                   # P = n T uniform
+    z = np.zeros(nx)
+    steps = int(round(0.01 / (kappa * k * k * dt)))
+    dens = {}
+    for alpha in (0.0, 0.2):
+        p = orc.Params(nx=nx, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=dt, tau_override=tau,
+                       alpha_override=alpha, model=model)
+        s = orc.init(p, n, T, z, z, z)
+        amp = []
+        for k_steps in (steps // 4, steps - steps // 4):
+            orc.step(s, k_steps)
+            m = orc.macroscopic(s)
+            amp.append(2.0 / nx * float(((m[0] / n0 - 1.0) * mode).sum()))
+        dens[alpha] = m[0].copy()
+        rate = math.log(amp[0] / amp[1]) / ((steps - steps // 4) * dt)
+        assert rate == pytest.approx(kappa * k * k, rel=0.03)
+        assert np.abs(m[2]).max() < 1e-12            # the gas stays at rest
+    # f is uniform up to the rounding of n T, so alpha reaches n only at that level
+    assert np.abs(dens[0.0] - dens[0.2]).max() < 1e-12 * n0
