@@ -30,6 +30,13 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
   N^x = sum c_x h with xi0 c0/c_t = 1) gives the diffusion coefficient
   tau_R (c0/c_t)^2 sum w' c_x^2 = tau/(3 sqrt(27)) on both lattices, with
   no lambda_i term (Sec. II.B): the result does not depend on alpha.
+* Sound attenuation: the longitudinal stress of the same expansion,
+  -tau_R (d/dt sum c_x^2 f^eq + (c0/c_t) d/dx sum c_x^3 f^eq), with
+  dP/dt = -(e + P) du/dx / 3, gives eta_L = tau_R 4 P ((c0/c_t)^2 m4/sigma2 - 1/3),
+  m4 = sum w c_x^4 (in the isotropic continuum this is 4 eta/3; on these
+  lattices 1.875 times that).  A standing sound wave decays at
+  eta_L k^2 / (2 (e + P)) in the limit dt -> 0; the time scheme takes away
+  damping as dt grows.
 """
 import math
 
@@ -208,3 +215,55 @@ def test_density_wave_diffuses_at_the_chapman_enskog_rate(orc, model, tau):
         assert np.abs(m[2]).max() < 1e-12            # the gas stays at rest
     # f is uniform up to the rounding of n T, so alpha reaches n only at that level
     assert np.abs(dens[0.0] - dens[0.2]).max() < 1e-12 * n0
+
+
+def _sound_decay(orc, model, tau, nx, dt, periods=6):
+    """fitted (decay rate, angular frequency) of a standing sound wave"""
+    from scipy.optimize import curve_fit
+    P0 = float(n_eq(1.0))
+    A = 1e-4
+    x = np.arange(nx)
+    k = 2 * math.pi / nx
+    mode = np.sin(k * (x + 0.5))
+    T = (1.0 + A * mode) ** 0.25
+    z = np.zeros(nx)
+    p = orc.Params(nx=nx, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=dt, tau_override=tau,
+                   alpha_override=0.0, model=model)
+    s = orc.init(p, n_eq(T), T, z, z, z)
+    om = CS * k
+    total = int(periods * 2 * math.pi / om / dt)
+    blk = max(total // 150, 1)
+    ts, amp = [], []
+    for i in range(total // blk):
+        orc.step(s, blk)
+        m = orc.macroscopic(s)
+        ts.append((i + 1) * blk * dt)
+        amp.append(2.0 / nx * float(((m[1] - 3.0 * P0) * mode).sum()) / (3.0 * P0 * A))
+    f = lambda t, a, g, o, ph: a * np.exp(-g * t) * np.cos(o * t + ph)
+    (a, g, o, ph), _ = curve_fit(f, np.array(ts), np.array(amp), p0=(1.0, 1e-3, om, 0.0))
+    return g, o
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("tau,tol", [(1.0, 0.06), (2.0, 0.04)])
+def test_sound_wave_decays_at_the_longitudinal_viscosity(orc, model, tau, tol):
+    pytest.importorskip("scipy")
+    e, c, w, wh, xi0 = orc.lattice(model)
+    sigma2 = float((w * c[:, 0] ** 2).sum())
+    m4 = float((w * c[:, 0] ** 4).sum())
+    m22 = float((w * c[:, 0] ** 2 * c[:, 1] ** 2).sum())
+    nu = orc.nu(model)
+    c0_ct = nu / math.sqrt(27.0)
+    tau_R = tau / (c0_ct * nu)
+    P0 = float(n_eq(1.0))
+    eta_L = tau_R * 4.0 * P0 * (c0_ct ** 2 * m4 / sigma2 - 1.0 / 3.0)
+    eta = tau_R * 4.0 * P0 * c0_ct ** 2 * m22 / sigma2
+    assert eta_L / (4.0 * eta / 3.0) == pytest.approx(1.875, rel=1e-12)
+    nx = 64
+    k = 2 * math.pi / nx
+    g, om = _sound_decay(orc, model, tau, nx, 0.05)
+    assert g == pytest.approx(eta_L * k * k / (2.0 * 4.0 * P0), rel=tol)
+    assert om == pytest.approx(CS * k, rel=3e-3)
+    # the time scheme takes damping away as dt grows
+    g25, _ = _sound_decay(orc, model, tau, nx, 0.25)
+    assert g25 < 0.75 * g
