@@ -105,3 +105,30 @@ def test_highly_relativistic_tube_converges_to_exact_solution(orc):
     errs = [_tube_error(orc, nx, 1000.0, 1, 0.2, 0.15) for nx in (200, 400, 800)]
     assert np.all(errs[1] < 0.8 * errs[0]) and np.all(errs[2] < 0.8 * errs[1]), errs
     assert np.all(errs[2] < [0.04, 0.2, 0.04]), errs[2]
+
+
+@pytest.mark.parametrize("case,tol", [("beta02", 0.005), ("beta09", 0.025)])
+def test_astrophysical_run_states_reach_the_printed_velocity(orc, case, tol):
+    """The slab and ambient states of the paper's 3-D run (Sec. III), in its
+    setting (Euler mode, alpha 0.2, dt/dx 0.15), on a 1-D tube: the gas
+    behind the shock moves at the exact plateau velocity, which the golden
+    file ties to the printed beta = 0.2 and 0.9."""
+    w = W.sphere_cloud(case, scale=1)
+    n0, T0 = w.inlet[0], w.inlet[1]
+    n1, T1 = w.solid[1], w.solid[2]
+    nx, steps, dt = 400, 800, 0.15
+    x = np.arange(nx)
+    slab = x < nx // 2
+    z = np.zeros(nx)
+    p = orc.Params(nx=nx, dt=dt, alpha_override=0.2, euler_mode=1)
+    st = orc.init(p, np.where(slab, n0, n1), np.where(slab, T0, T1), z, z, z)
+    orc.step(st, steps)
+    assert st.nonphysical == 0
+    m = orc.macroscopic(st)
+    sol = R.solve(n0 * T0, 0.0, n0, n1 * T1, 0.0, n1)
+    _, v, _ = sol.sample((x + 0.5 - nx // 2) / (steps * dt))
+    plateau = np.abs(v - sol.vstar) < 1e-12
+    assert plateau.sum() > 30
+    assert abs(float(np.median(m[2][plateau])) - sol.vstar) < tol
+    printed = {"beta02": 0.2, "beta09": 0.9}[case]
+    assert abs(sol.vstar - printed) < 0.015
