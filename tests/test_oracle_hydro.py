@@ -30,6 +30,10 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
   N^x = sum c_x h with xi0 c0/c_t = 1) gives the diffusion coefficient
   tau_R (c0/c_t)^2 sum w' c_x^2 = tau/(3 sqrt(27)) on both lattices, with
   no lambda_i term (Sec. II.B): the result does not depend on alpha.
+* Anisotropy: sum_i w_i c_a c_b c_c c_d is cubic, not isotropic, on these
+  lattices (m4 != 3 m22), so the shear viscosity depends on direction: a
+  shear wave with k along (1, 1, 0) and u along (1, -1, 0) sees
+  eta (1 + (m4 - 3 m22)/(2 m22)), 1.875 eta on both lattices.
 * Sound attenuation: the longitudinal stress of the same expansion,
   -tau_R (d/dt sum c_x^2 f^eq + (c0/c_t) d/dx sum c_x^3 f^eq), with
   dP/dt = -(e + P) du/dx / 3, gives eta_L = tau_R 4 P ((c0/c_t)^2 m4/sigma2 - 1/3),
@@ -267,3 +271,46 @@ def test_sound_wave_decays_at_the_longitudinal_viscosity(orc, model, tau, tol):
     # the time scheme takes damping away as dt grows
     g25, _ = _sound_decay(orc, model, tau, nx, 0.25)
     assert g25 < 0.75 * g
+
+
+def _shear_rate_2d(orc, model, L, diagonal, tau=1.0, frac=0.05, guess=1.0):
+    """fitted decay rate of a 2-D shear wave along x or along (1, 1)"""
+    yy, xx = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    A = 1e-4
+    if diagonal:
+        ph = 2 * math.pi * (xx + yy + 1.0) / L
+        k2 = 2 * (2 * math.pi / L) ** 2
+        ux = A * np.sin(ph) / math.sqrt(2.0)
+        uy = -ux
+    else:
+        ph = 2 * math.pi * (xx + 0.5) / L
+        k2 = (2 * math.pi / L) ** 2
+        ux = np.zeros((L, L))
+        uy = A * np.sin(ph)
+    N = L * L
+    T = np.ones(N)
+    p = orc.Params(nx=L, ny=L, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=0.25, tau_override=tau,
+                   alpha_override=0.0, model=model)
+    s = orc.init(p, n_eq(T), T, ux.reshape(-1), uy.reshape(-1), np.zeros(N))
+    steps = int(round(frac / (guess * k2 * 0.25)))
+    skip = max(steps // 4, 16)                   # the viscous stress builds up over ~tau_R
+    amp = []
+    for k_steps in (skip, steps):
+        orc.step(s, k_steps)
+        m = orc.macroscopic(s)
+        v = (m[2] - m[3]) / math.sqrt(2.0) if diagonal else m[3]
+        amp.append(2.0 / N * float((v.reshape(L, L) * np.sin(ph)).sum()))
+    return math.log(amp[0] / amp[1]) / (steps * 0.25)
+
+
+@pytest.mark.parametrize("model,L,tol", [(0, 64, 0.06), (1, 64, 0.06)])
+def test_shear_viscosity_is_anisotropic(orc, model, L, tol):
+    e, c, w, wh, xi0 = orc.lattice(model)
+    m4 = float((w * c[:, 0] ** 4).sum())
+    m22 = float((w * c[:, 0] ** 2 * c[:, 1] ** 2).sum())
+    factor = 1.0 + (m4 - 3.0 * m22) / (2.0 * m22)
+    assert factor == pytest.approx(1.875, rel=1e-12)
+    g_axis = _shear_rate_2d(orc, model, L, False, guess=0.06)
+    g_diag = _shear_rate_2d(orc, model, L, True, guess=0.11)
+    # both waves have |k| chosen so that the ratio of rates is the ratio of viscosities x 2
+    assert g_diag / (2.0 * g_axis) == pytest.approx(factor, rel=tol)
