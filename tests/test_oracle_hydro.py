@@ -37,8 +37,8 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
 * Sound attenuation: the longitudinal stress of the same expansion,
   -tau_R (d/dt sum c_x^2 f^eq + (c0/c_t) d/dx sum c_x^3 f^eq), with
   dP/dt = -(e + P) du/dx / 3, gives eta_L = tau_R 4 P ((c0/c_t)^2 m4/sigma2 - 1/3),
-  m4 = sum w c_x^4 (in the isotropic continuum this is 4 eta/3; on these
-  lattices 1.875 times that).  A standing sound wave decays at
+  m4 = sum w c_x^4 (for massless particles in the continuum this is
+  4 eta/3; on these lattices 1.875 times that).  A standing sound wave decays at
   eta_L k^2 / (2 (e + P)) in the limit dt -> 0; the time scheme takes away
   damping as dt grows.
 """
