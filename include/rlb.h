@@ -153,6 +153,11 @@ RLB_API rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over
  * Eq. 41 with the entropy s = n (4 - ln lambda) of Sec. III (the factor
  * 4 - ln lambda floored at 1e-3); zeta_over_s sets alpha through Eq. 56 at the
  * reference state T = 1, lambda = 1 unless opts->alpha_override >= 0.
+ * The step itself (limited-flux streaming, implicit collision) realises a
+ * shear viscosity proportional to tau with no -1/2 shift: 0.2369 P tau
+ * (extended lattice) or 0.1621 P tau (basic), larger along face diagonals;
+ * and the alpha term diffuses momentum with 2.50 alpha (extended) per unit
+ * time, adding a viscosity 2.50 alpha (e + P).
  * opts may be NULL (defaults).  Allocates 2 x 38 population planes, 5
  * previous-level planes and scratch on the device; *out receives the handle
  * (NULL on failure).  Errors: RLB_E_INVALID, RLB_E_UNSTABLE, RLB_E_NOMEM,
