@@ -113,3 +113,28 @@ def test_oracle_is_used_only_by_the_baseline_legs_and_the_entry_checks():
             if fn.endswith((".cu", ".cuh", ".h", ".cpp")):
                 text = open(os.path.join(dirpath, fn)).read()
                 assert "rlb_oracle" not in text and "orc_" not in text, fn
+
+
+def test_reference_arm_line_has_the_contract_keys(capsys, monkeypatch):
+    """`bench.py --impl reference` (the oracle on the host cores) prints one
+    JSON line with the benchmark's keys, the reference marker, its CPU
+    baseline and an end-to-end entry without host copies"""
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    args = type("A", (), {"steps": 2, "warmup": 1, "gpus": 1})()
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+                "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["steps"] == 2 and line["warmup"] == 1
+    assert line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["value"] > 0 and line["higher_is_better"] is True
+    assert set(line["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert "workload" in line["config"]
