@@ -212,3 +212,17 @@ def test_binding_signatures_match_the_header(lib):
             assert fn.restype is None, name
         else:
             assert _ctype_matches(ret + " r", fn.restype), (name, ret, fn.restype)
+
+
+def test_no_gpu_means_an_error_not_a_fallback(lib):
+    """without a CUDA device the library reports RLB_E_CUDA for a valid
+    configuration: there is no CPU path to fall back on"""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(rlb.RLBError) as e:
+        rlb.Grid(16)
+    assert e.value.status == rlb.RLB_E_CUDA
+    with pytest.raises(rlb.RLBError) as e:
+        rlb.Batch([64, 32], [0.1, 0.1], [0.0, 0.0])
+    assert e.value.status == rlb.RLB_E_CUDA
