@@ -226,3 +226,21 @@ def test_no_gpu_means_an_error_not_a_fallback(lib):
     with pytest.raises(rlb.RLBError) as e:
         rlb.Batch([64, 32], [0.1, 0.1], [0.0, 0.0])
     assert e.value.status == rlb.RLB_E_CUDA
+
+
+def test_a_c_program_uses_the_abi(lib, tmp_path):
+    """tests/c/shock_tube.c builds against include/rlb.h and librlb.so with a
+    plain C compiler and runs: the host-side check passes, and without a GPU
+    rlb_create reports RLB_E_CUDA, which the program prints before it exits 0"""
+    exe = tmp_path / "shock_tube"
+    libdir = os.path.dirname(rlb.LIB_PATH)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    "-o", str(exe), os.path.join(ROOT, "tests", "c", "shock_tube.c"),
+                    "-L", libdir, "-l:librlb.so", f"-Wl,-rpath,{libdir}", "-lm"], check=True)
+    torch = pytest.importorskip("torch")
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    if not torch.cuda.is_available():
+        assert r.stdout.startswith("no CUDA device: RLB_E_CUDA"), r.stdout
+    else:
+        assert "u_x at the membrane" in r.stdout
