@@ -247,14 +247,28 @@ def rlb_state_bytes(ctx) -> int:
     return int(lib().rlb_state_bytes(ctx))
 
 
+def _state_buffer(buf, nbytes: int) -> int:
+    """address of a contiguous numpy array or torch tensor holding at least
+    nbytes; raises rather than let the library overrun a short buffer"""
+    if hasattr(buf, "data_ptr"):
+        size, contiguous, ptr = buf.numel() * buf.element_size(), buf.is_contiguous(), buf.data_ptr()
+    else:
+        size, contiguous, ptr = buf.nbytes, buf.flags.c_contiguous, buf.ctypes.data
+    if not contiguous:
+        raise ValueError("the state buffer must be contiguous")
+    if size < nbytes:
+        raise ValueError(f"the state buffer holds {size} bytes; the state needs {nbytes}")
+    return ptr
+
+
 def rlb_get_state(ctx, buf, on_device: int):
-    ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
-    _check(lib().rlb_get_state(ctx, ptr, rlb_state_bytes(ctx), int(on_device)), ctx)
+    nbytes = rlb_state_bytes(ctx)
+    _check(lib().rlb_get_state(ctx, _state_buffer(buf, nbytes), nbytes, int(on_device)), ctx)
 
 
 def rlb_set_state(ctx, buf, on_device: int):
-    ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else buf.ctypes.data
-    _check(lib().rlb_set_state(ctx, ptr, rlb_state_bytes(ctx), int(on_device)), ctx)
+    nbytes = rlb_state_bytes(ctx)
+    _check(lib().rlb_set_state(ctx, _state_buffer(buf, nbytes), nbytes, int(on_device)), ctx)
 
 
 def rlb_set_stream(ctx, stream):

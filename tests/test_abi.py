@@ -8,6 +8,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 from paper_1302_1125_gb300 import build as B
@@ -246,3 +247,19 @@ def test_a_c_program_uses_the_abi(lib, tmp_path):
         # the gas at the membrane moves at the exact plateau velocity, 0.191
         ux = float(r.stdout.split("u_x at the membrane:")[1].split()[0])
         assert abs(ux - 0.191) < 0.005, r.stdout
+
+
+def test_state_buffers_are_checked_before_the_library_sees_them():
+    """the binding refuses a short or non-contiguous checkpoint buffer
+    instead of letting rlb_get_state write past its end"""
+    ok = np.zeros(43 * 10, np.float32)
+    assert rlb._state_buffer(ok, ok.nbytes) == ok.ctypes.data
+    with pytest.raises(ValueError, match="holds"):
+        rlb._state_buffer(np.zeros(43 * 10 - 1, np.float32), ok.nbytes)
+    with pytest.raises(ValueError, match="contiguous"):
+        rlb._state_buffer(np.zeros(2 * 43 * 10, np.float32)[::2], ok.nbytes)
+    torch = pytest.importorskip("torch")
+    t = torch.zeros(43 * 10, dtype=torch.float32)
+    assert rlb._state_buffer(t, ok.nbytes) == t.data_ptr()
+    with pytest.raises(ValueError, match="holds"):
+        rlb._state_buffer(t[:-1], ok.nbytes)
