@@ -336,6 +336,8 @@ class Grid:
         if hasattr(mask, "is_cuda") and mask.is_cuda:
             torch = _torch()
             m = (mask.reshape(-1) != 0).to(torch.uint8).contiguous()
+            if m.numel() != self.N:
+                raise ValueError(f"mask has {m.numel()} values, expected {self.N}")
             _check(lib().rlb_set_solid(self.ctx, m.data_ptr(), float(n), float(T), 1), self.ctx)
         else:
             m = np.ascontiguousarray(np.asarray(mask).reshape(-1) != 0, np.uint8)
@@ -433,8 +435,9 @@ class Batch:
                  tau_override=0.0, alpha_override=-1.0, symmetry_1d=0, stream="current"):
         self.nx = _i32(nx)
         self.B = int(self.nx.size)
-        self.eta = np.ascontiguousarray(eta_over_s, np.float64)
-        self.zeta = np.ascontiguousarray(zeta_over_s, np.float64)
+        # one value per tube (a scalar applies to all); the library reads B of each
+        self.eta = np.ascontiguousarray(np.broadcast_to(np.asarray(eta_over_s, np.float64), (self.B,)))
+        self.zeta = np.ascontiguousarray(np.broadcast_to(np.asarray(zeta_over_s, np.float64), (self.B,)))
         s = _current_stream() if stream == "current" else stream
         self._opts = make_options(dt_over_dx, tau_override, alpha_override, 0, FP32_STORAGE, s, symmetry_1d)
         h = C.c_void_p()

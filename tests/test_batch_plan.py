@@ -166,3 +166,18 @@ def test_batch_null_handles_are_rejected():
     assert L.rlb_batch_init(None, None, None, None, 0) == rlb.RLB_E_INVALID
     assert L.rlb_batch_total_cells(None) == 0
     L.rlb_batch_destroy(None)
+
+
+def test_batch_parameters_are_sized_before_the_library_reads_them():
+    """the binding broadcasts eta/s and zeta/s to one value per tube and
+    refuses arrays of another length (the library reads B values of each)"""
+    with pytest.raises(ValueError):
+        rlb.Batch([64, 80, 96], [0.1, 0.2], [0.0, 0.0, 0.0])
+    with pytest.raises(ValueError):
+        rlb.Batch([64, 80], [0.1, 0.2], [0.0, 0.0, 0.0])
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        # sizes accepted: the call reaches the library, which needs a device
+        with pytest.raises(rlb.RLBError) as e:
+            rlb.Batch([64, 80], 0.1, 0.0)
+        assert e.value.status == rlb.RLB_E_CUDA
