@@ -415,8 +415,9 @@ def _i64(a):
 
 def rlb_batch_plan(nx, nsteps, tuning, nclusters):
     """Host-side job plan (see rlb.h): (order, jobs[njobs, 4], cl_start, critical)."""
-    nx, st = _i32(nx), _i64(nsteps)
+    nx = _i32(nx)
     B = nx.size
+    st = _i64(np.broadcast_to(np.asarray(nsteps, np.int64), (B,)))   # the library reads B counts
     order = np.zeros(B, np.int32)
     jobs = np.zeros(4 * B, np.int32)
     cl = np.zeros(int(nclusters) + 1, np.int32)

@@ -181,3 +181,10 @@ def test_batch_parameters_are_sized_before_the_library_reads_them():
         with pytest.raises(rlb.RLBError) as e:
             rlb.Batch([64, 80], 0.1, 0.0)
         assert e.value.status == rlb.RLB_E_CUDA
+
+
+def test_plan_step_counts_are_sized_before_the_library_reads_them():
+    t = rlb.rlb_batch_tuning(256, 256, 1, 1, 0.0)
+    with pytest.raises(ValueError):
+        rlb.rlb_batch_plan([64, 80, 96], [10, 20], t, 4)
+    assert rlb.rlb_batch_plan([64, 80, 96], 10, t, 4)[3] == 10     # a scalar applies to all tubes
