@@ -34,6 +34,10 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
   lattices (m4 != 3 m22), so the shear viscosity depends on direction: a
   shear wave with k along (1, 1, 0) and u along (1, -1, 0) sees
   eta (1 + (m4 - 3 m22)/(2 m22)), 1.875 eta on both lattices.
+* Euler mode (Sec. III: f and h set to the equilibria of the streamed state
+  every step) carries no viscosity of its own: a shear wave decays only
+  through the limiter's numerical viscosity, which does not depend on dt,
+  halves when the resolution doubles and is far below the viscous mode's.
 * Sound attenuation: the longitudinal stress of the same expansion,
   -tau_R (d/dt sum c_x^2 f^eq + (c0/c_t) d/dx sum c_x^3 f^eq), with
   dP/dt = -(e + P) du/dx / 3, gives eta_L = tau_R 4 P ((c0/c_t)^2 m4/sigma2 - 1/3),
@@ -314,3 +318,30 @@ def test_shear_viscosity_is_anisotropic(orc, model, L, tol):
     g_diag = _shear_rate_2d(orc, model, L, True, guess=0.11)
     # both waves have |k| chosen so that the ratio of rates is the ratio of viscosities x 2
     assert g_diag / (2.0 * g_axis) == pytest.approx(factor, rel=tol)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_euler_mode_is_inviscid_up_to_the_limiter(orc, model):
+    A = 1e-4
+    etas = {}
+    for nx, dt in ((128, 0.25), (256, 0.25), (128, 0.1)):
+        x = np.arange(nx)
+        k = 2 * math.pi / nx
+        mode = np.sin(k * (x + 0.5))
+        T = np.ones(nx)
+        z = np.zeros(nx)
+        p = orc.Params(nx=nx, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=dt, alpha_override=0.0,
+                       euler_mode=1, model=model)
+        s = orc.init(p, n_eq(T), T, z, A * mode, z)
+        steps = int(round(0.5 * nx * nx / (dt * 256)))
+        amp = []
+        for k_steps in (16, steps):
+            orc.step(s, k_steps)
+            amp.append(2.0 / nx * float((orc.macroscopic(s)[3] * mode).sum()))
+        rate = math.log(amp[0] / amp[1]) / (steps * dt)
+        etas[nx, dt] = rate * 4.0 * float(n_eq(1.0)) / k ** 2
+    P0 = float(n_eq(1.0))
+    viscous = 0.2369 * P0 * 1.0 if model == 0 else 0.1621 * P0 * 1.0     # tau = 1
+    assert 0.0 < etas[256, 0.25] < 0.03 * viscous
+    assert 0.4 < etas[256, 0.25] / etas[128, 0.25] < 0.6                 # first order in dx
+    assert etas[128, 0.1] == pytest.approx(etas[128, 0.25], rel=0.05)    # no dependence on dt
