@@ -108,3 +108,83 @@ def test_check_config_counts_cells_in_64_bits():
     assert rlb.rlb_check_config(g, 19, 0.1, 0.0, 0, rlb.make_options()) == rlb.RLB_OK
     g = rlb.make_grid(1024, 1024, 1024, (0, 0, 0), (0, 0, 0), (1.0, 1.0, (0.0, 0.0, 0.0)))   # 2^30
     assert rlb.rlb_check_config(g, 19, 0.1, 0.0, 0, rlb.make_options(dt_over_dx=0.15)) == rlb.RLB_OK
+
+
+def batch_expected(nx, eta, zeta, limiter, o):
+    """the statuses rlb_batch_create may return under the header's rules
+    (their order is not specified, so both when both kinds apply); a valid
+    batch reaches the device and, without one, fails with RLB_E_CUDA"""
+    B = len(nx)
+    invalid = not (1 <= B <= 65535)
+    invalid |= o["precision"] != 1 or o["euler"] != 0 or o["sym1"] not in (0, 1) or o["model"] != 0
+    invalid |= limiter not in (0, 1)
+    invalid |= not (o["dt"] > 0 and math.isfinite(o["dt"]))
+    invalid |= not (math.isfinite(o["tau"]) and math.isfinite(o["alpha"]))
+    invalid |= any(n < 1 for n in nx)
+    invalid |= any(not (v >= 0 and math.isfinite(v)) for v in list(eta) + list(zeta))
+    invalid |= sum(-(-max(n, 0) // 32) * 32 for n in nx) > 2 ** 30
+    nu = math.sqrt(13.0)
+    c0ct = nu / math.sqrt(27.0)
+    unstable = False
+    if math.isfinite(o["dt"]) and o["dt"] > 0:
+        unstable |= 2 * c0ct * o["dt"] > 1.0
+        for z in zeta:
+            alpha = o["alpha"] if o["alpha"] >= 0 else 27.0 * z / nu ** 6
+            unstable |= 2 * c0ct * nu * o["dt"] * alpha > 1.0
+    got = set()
+    if invalid:
+        got.add(rlb.RLB_E_INVALID)
+    if unstable:
+        got.add(rlb.RLB_E_UNSTABLE)
+    return got or {rlb.RLB_E_CUDA}
+
+
+@hyp.settings(max_examples=2000, deadline=None, derandomize=True)
+@hyp.given(nx=st.lists(st.sampled_from([0, 1, 33, 800, 8192]), min_size=0, max_size=4),
+           eta=st.sampled_from([-0.1, 0.0, 0.1, math.inf, math.nan]),
+           zeta=st.sampled_from([0.0, 0.05, 1e4, 1e6, -1.0, math.nan]),
+           limiter=st.sampled_from([0, 1, 2]),
+           dt=st.sampled_from([0.0, 0.15, 0.25, 0.5, 0.8, math.nan]),
+           precision=st.sampled_from([0, 1]), euler=st.sampled_from([0, 1]),
+           sym1=st.sampled_from([0, 1, 2]), model=st.sampled_from([0, 1]),
+           tau=st.sampled_from([0.0, 0.8, math.inf]),
+           alpha=st.sampled_from([-1.0, 0.0, 0.2, 2.0, math.nan]))
+def test_batch_create_follows_the_documented_rules(nx, eta, zeta, limiter, dt, precision, euler, sym1,
+                                                   model, tau, alpha):
+    import ctypes as C
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a valid batch would allocate on the device")
+    o = dict(dt=dt, precision=precision, euler=euler, sym1=sym1, model=model, tau=tau, alpha=alpha)
+    B = len(nx)
+    n_arr = np.asarray(nx if B else [1], np.int32)
+    e_arr = np.full(max(B, 1), eta, np.float64)
+    z_arr = np.full(max(B, 1), zeta, np.float64)
+    opts = rlb.make_options(dt, tau, alpha, euler, precision, None, symmetry_1d=sym1, model=model)
+    h = C.c_void_p()
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    got = rlb.lib().rlb_batch_create(B, n_arr.ctypes.data_as(ip), e_arr.ctypes.data_as(dp),
+                                     z_arr.ctypes.data_as(dp), limiter, C.byref(opts), C.byref(h))
+    assert h.value is None
+    assert got in batch_expected(nx, [eta] * B, [zeta] * B, limiter, o)
+
+
+@pytest.mark.parametrize("B,n,expect", [(65536, 1, rlb.RLB_E_INVALID), (2, 1 << 29, rlb.RLB_E_CUDA),
+                                        (3, 1 << 29, rlb.RLB_E_INVALID), (2, (1 << 29) + 1, rlb.RLB_E_INVALID)])
+def test_batch_create_size_limits(B, n, expect):
+    """B <= 65535; at most 2^30 stored cells, each tube rounded up to 32 cells"""
+    import ctypes as C
+    import numpy as np
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a valid batch would allocate on the device")
+    nx = np.full(B, n, np.int32)
+    eta = np.full(B, 0.1)
+    zeta = np.zeros(B)
+    opts = rlb.make_options(dt_over_dx=0.15, precision=rlb.FP32_STORAGE)
+    h = C.c_void_p()
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int)
+    got = rlb.lib().rlb_batch_create(B, nx.ctypes.data_as(ip), eta.ctypes.data_as(dp), zeta.ctypes.data_as(dp),
+                                     0, C.byref(opts), C.byref(h))
+    assert got == expect and h.value is None
