@@ -318,8 +318,9 @@ typedef struct {
  * through Eq. 56 per tube, as in rlb_create; opts->alpha_override >= 0 sets
  * one alpha for all tubes).  opts may be NULL: defaults of
  * rlb_default_options with precision RLB_FP32_STORAGE.  Requirements:
- * precision RLB_FP32_STORAGE, euler_mode 0, symmetry_1d 0 or 1 (the tubes are
- * 1-D with u_y = u_z = 0, so the reduction is exact), at most 2^30 stored cells
+ * precision RLB_FP32_STORAGE, euler_mode 0, model 0, symmetry_1d 0 or 1 (the
+ * tubes are 1-D with u_y = u_z = 0, so the reduction is exact; thread_mapping
+ * and symmetry_2d do not apply to tubes and are ignored), at most 2^30 stored cells
  * (each tube stored from a 128-byte boundary).  RLB_E_UNSTABLE if
  * 2 (c_0/c_t) dt/dx > 1 or 2 (c_0 nu / c_t) dt alpha_b > 1 for a tube.
  * Allocates 81 population and previous-level planes over the stored cells
