@@ -138,3 +138,13 @@ def test_reference_arm_line_has_the_contract_keys(capsys, monkeypatch):
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
     assert "workload" in line["config"]
+
+
+def test_peak_bandwidth_is_the_measured_one_else_the_fallback(tmp_path, monkeypatch):
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6778.0, "bf16_tflops": 1873.2}')
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.peaks() == (6778.0, "measured")
+    (tmp_path / "MEASURED_PEAKS.json").unlink()
+    assert bench.peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text("{not json")
+    assert bench.peaks() == (6800.0, "fallback")
