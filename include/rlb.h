@@ -148,8 +148,8 @@ RLB_API void rlb_default_options(rlb_options *opts);
  * (d = number of axes with more than one cell, at least 1).  These bounds are
  * necessary, not sufficient: the time scheme takes damping away from sound
  * waves as dt/dx grows, so with little viscosity and alpha = 0 they can grow
- * inside the bounds (a 1-D tube with tau ~ 1.15 does at dt/dx = 0.36, not at
- * 0.25); the alpha term restores the damping. */
+ * inside the bounds: long sound waves stay damped only below about
+ * dt/dx = 0.21 tau.  The alpha term restores the damping. */
 RLB_API rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s,
                             double zeta_over_s, int limiter, const rlb_options *opts);
 
