@@ -675,7 +675,7 @@ def run_ours(args):
     return 0
 
 
-def main():
+def arg_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
@@ -683,7 +683,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched sweep, the sphere-cloud run and the basic-model runs")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = arg_parser().parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

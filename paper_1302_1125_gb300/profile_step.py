@@ -62,7 +62,7 @@ def run_batch(a):
                       "tuning": t.as_dict(), "resident_clusters": ncl}))
 
 
-def main():
+def arg_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cloud_3d", choices=sorted(MAKERS))
     ap.add_argument("--scale", type=int, default=1)
@@ -71,7 +71,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--tuning", default="", help="batch launch shape threads,bound,cluster,pairs_per_thread")
     ap.add_argument("--symmetry", action="store_true", help="batch: the 1-D symmetry reduction")
-    a = ap.parse_args()
+    return ap
+
+
+def main():
+    a = arg_parser().parse_args()
     B.build()
     if a.workload == "batch_tubes":
         return run_batch(a)

@@ -148,3 +148,32 @@ def test_peak_bandwidth_is_the_measured_one_else_the_fallback(tmp_path, monkeypa
     assert bench.peaks() == (6800.0, "fallback")
     (tmp_path / "MEASURED_PEAKS.json").write_text("{not json")
     assert bench.peaks() == (6800.0, "fallback")
+
+
+def _quoted_commands():
+    """(module, argv) of every bench.py or profile_step command the committed
+    profile summaries quote"""
+    import re
+    import shlex
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    found = []
+    for name in sorted(os.listdir(os.path.join(root, "profiles"))):
+        for ln in open(os.path.join(root, "profiles", name)):
+            m = re.search(r"python (-m paper_1302_1125_gb300\.profile_step|bench\.py)((?: --?[\w-]+(?: [\w.,]+)?)*)", ln)
+            if m:
+                found.append((name, "profile_step" if "profile_step" in m.group(1) else "bench",
+                              shlex.split(m.group(2))))
+    return found
+
+
+def test_profile_commands_parse_with_the_committed_clis():
+    """every command quoted in profiles/ uses only options that the committed
+    bench.py and profile_step accept"""
+    from paper_1302_1125_gb300 import profile_step
+    cmds = _quoted_commands()
+    assert {m for _, m, _ in cmds} == {"bench", "profile_step"}
+    for name, module, argv in cmds:
+        parser = bench.arg_parser() if module == "bench" else profile_step.arg_parser()
+        parser.exit = lambda status=0, message=None: (_ for _ in ()).throw(AssertionError((name, argv, message)))
+        parser.error = lambda message: (_ for _ in ()).throw(AssertionError((name, argv, message)))
+        parser.parse_args(argv)
