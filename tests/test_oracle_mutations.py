@@ -15,7 +15,8 @@ mistyped weight, doubled diagonals, swapped number weights; Euler mode
 (Sec. III) taking the equilibria of the unstreamed state; the bulk term of
 Eq. 57 applied to the number distribution as well; an inlet ghost whose
 pressure drops the temperature; open ends that reflect instead of copying
-the edge cell.
+the edge cell; the h equation relaxing to h^eq(t) instead of the
+extrapolated 2 h^eq(t) - h^eq(t - dt).
 """
 import os
 import subprocess
@@ -68,6 +69,9 @@ MUTATIONS = {
                                  "orc_feq(p->inlet_n, up, k->ghost_f);"),
     "outflow_ghosts_reflecting": ("if (bc == ORC_BC_OUTFLOW) return c < 0 ? 0 : n - 1;",
                                   "if (bc == ORC_BC_OUTFLOW) return c < 0 ? -c : 2 * n - 2 - c;"),
+    "number_equilibrium_not_extrapolated": (
+        "ho[i] = (h[i] + sh[i] + omega * (2.0 * heq[i] - heqp[i])) / (1.0 + omega);",
+        "ho[i] = (h[i] + sh[i] + omega * heq[i]) / (1.0 + omega);"),
     "minmod_takes_larger_slope": ("return 0.5 * fmin(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));",
                                   "return 0.5 * fmax(fabs(X), fabs(Y)) * (sgn(X) + sgn(Y));"),
 }
