@@ -33,7 +33,9 @@ statements of Sec. II.B and Sec. III, not by its own formulas:
 * Anisotropy: sum_i w_i c_a c_b c_c c_d is cubic, not isotropic, on these
   lattices (m4 != 3 m22), so the shear viscosity depends on direction: a
   shear wave with k along (1, 1, 0) and u along (1, -1, 0) sees
-  eta (1 + (m4 - 3 m22)/(2 m22)), 1.875 eta on both lattices.
+  eta (1 + (m4 - 3 m22)/(2 m22)), 1.875 eta on both lattices.  Particle
+  diffusion needs only sum w' c_a c_b = delta_ab/3 and is isotropic: a
+  density wave along (1, 1, 0) diffuses at the rate of one along x.
 * Euler mode (Sec. III: f and h set to the equilibria of the streamed state
   every step) carries no viscosity of its own: a shear wave decays only
   through the limiter's numerical viscosity, which does not depend on dt,
@@ -345,3 +347,32 @@ def test_euler_mode_is_inviscid_up_to_the_limiter(orc, model):
     assert 0.0 < etas[256, 0.25] < 0.03 * viscous
     assert 0.4 < etas[256, 0.25] / etas[128, 0.25] < 0.6                 # first order in dx
     assert etas[128, 0.1] == pytest.approx(etas[128, 0.25], rel=0.05)    # no dependence on dt
+
+
+def _density_rate_2d(orc, model, L, diagonal, tau=1.0, dt=0.25):
+    """fitted decay rate of a 2-D density wave at uniform pressure, along x or (1, 1)"""
+    yy, xx = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    ph = 2 * math.pi * ((xx + yy + 1.0) if diagonal else (xx + 0.5)) / L
+    k2 = (2 if diagonal else 1) * (2 * math.pi / L) ** 2
+    n0 = float(n_eq(1.0))
+    n = n0 * (1.0 + 1e-3 * np.sin(ph)).reshape(-1)
+    N = L * L
+    z = np.zeros(N)
+    p = orc.Params(nx=L, ny=L, bc_lo=(0, 0, 0), bc_hi=(0, 0, 0), dt=dt, tau_override=tau,
+                   alpha_override=0.0, model=model)
+    s = orc.init(p, n, n0 / n, z, z, z)
+    steps = int(round(0.03 / (tau / (3 * math.sqrt(27.0)) * k2 * dt)))
+    amp = []
+    for k_steps in (max(steps // 4, 16), steps):
+        orc.step(s, k_steps)
+        m = orc.macroscopic(s)
+        amp.append(2.0 / N * float(((m[0] / n0 - 1.0).reshape(L, L) * np.sin(ph)).sum()))
+    return math.log(amp[0] / amp[1]) / (steps * dt) / k2
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_particle_diffusion_is_isotropic(orc, model):
+    axis = _density_rate_2d(orc, model, 64, False)
+    diag = _density_rate_2d(orc, model, 64, True)
+    assert diag == pytest.approx(axis, rel=0.01)
+    assert axis == pytest.approx(1.0 / (3 * math.sqrt(27.0)), rel=0.1)     # tau = 1
