@@ -69,3 +69,17 @@ def test_shared_constants(orc):
     assert env["kPi2Over16"] == pytest.approx(math.pi ** 2 / 16.0, rel=1e-15)     # 1/(d_G/pi^2)
     assert env["kXi0"] == pytest.approx(xi0, rel=1e-15)
     assert env["kOmegaC"] == pytest.approx(13.0 / math.sqrt(27.0), rel=1e-15)
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_velocity_table_matches_the_oracle(orc, model):
+    """kDir of rlb_device.cuh (the extended lattice's integer vectors, population
+    order rest, axes, diagonals; the basic lattice halves the diagonals)"""
+    text = open(os.path.join(os.path.dirname(SRC), "rlb_device.cuh")).read()
+    m = re.search(r"constexpr Dir kDir\[19\] = \{(.*?)\};", text, re.S)
+    assert m
+    kdir = np.array([int(v) for v in re.findall(r"-?\d+", m.group(1))]).reshape(19, 3)
+    if model == 1:
+        kdir[7:] //= 2
+    e, c, w, wh, xi0 = orc.lattice(model)
+    assert np.array_equal(kdir, np.rint(c).astype(int)) and np.allclose(c, kdir, rtol=0, atol=1e-15)
