@@ -132,3 +132,20 @@ def test_astrophysical_run_states_reach_the_printed_velocity(orc, case, tol):
     assert abs(float(np.median(m[2][plateau])) - sol.vstar) < tol
     printed = {"beta02": 0.2, "beta09": 0.9}[case]
     assert abs(sol.vstar - printed) < 0.015
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_exact_solver_weak_shock_limit(eps):
+    """As the pressure jump P_L/P_R = 1 + eps vanishes the solution becomes
+    linear acoustics of the e = 3P gas: the plateau moves at
+    u* = (P_L - P_R)/(2 w c_s) (impedance w c_s, w = e + P = 4P), the
+    rarefaction head at -c_s, and the shock at the mean of the characteristic
+    speeds ahead (c_s) and behind ((u* + c_s)/(1 + u* c_s)), i.e.
+    c_s + u*/3 = c_s (1 + eps/8) to first order."""
+    cs = 1.0 / np.sqrt(3.0)
+    PL = 1.0 + eps
+    s = R.solve(PL, 0.0, 1.0, 1.0, 0.0, 1.0)
+    w = 4.0 * (1.0 + eps / 2.0)
+    assert s.vstar == pytest.approx((PL - 1.0) / (2.0 * w * cs), rel=100 * eps ** 2)
+    assert s.left_speeds[0] == pytest.approx(-cs, rel=1e-12)
+    assert (s.right_speeds[0] / cs - 1.0) / eps == pytest.approx(1.0 / 8.0, rel=0.01)
