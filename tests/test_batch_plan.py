@@ -188,3 +188,19 @@ def test_plan_step_counts_are_sized_before_the_library_reads_them():
     with pytest.raises(ValueError):
         rlb.rlb_batch_plan([64, 80, 96], [10, 20], t, 4)
     assert rlb.rlb_batch_plan([64, 80, 96], 10, t, 4)[3] == 10     # a scalar applies to all tubes
+
+
+def test_batch_from_spec_marshals_through_to_the_library():
+    """the 512-tube recipe's arrays pass the binding's checks and reach
+    rlb_batch_create (which, without a device, answers RLB_E_CUDA)"""
+    from paper_1302_1125_gb300 import workloads as W
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    for spec in (W.batch_tubes(), W.batch_tubes(count=8, seed=3)):
+        with pytest.raises(rlb.RLBError) as e:
+            rlb.Batch.from_spec(spec)
+        assert e.value.status == rlb.RLB_E_CUDA
+        with pytest.raises(rlb.RLBError) as e:
+            rlb.Batch.from_spec(spec, symmetry_1d=1)
+        assert e.value.status == rlb.RLB_E_CUDA
