@@ -181,3 +181,23 @@ def test_periodic_box_gamma_bound():
         gam = 1.0 / np.sqrt(1.0 - (ux * ux + uy * uy + uz * uz))
         assert gam.max() <= 3.0
         assert w.bc_lo == (W.BC_PERIODIC,) * 3 and w.bc_hi == (W.BC_PERIODIC,) * 3
+
+
+@pytest.mark.parametrize("make,kw", [
+    (W.tube_800, {}), (W.tube_800, {"symmetry_1d": 1}), (lambda: W.tube_8192("a"), {}),
+    (lambda: W.tube_8192("b"), {}), (W.cloud_2d, {}), (W.cloud_2d, {"symmetry_2d": 1}),
+    (W.cloud_3d, {}), (lambda: W.sphere_cloud("beta02", viscous=True), {}),
+    (lambda: W.sphere_cloud("beta09"), {}), (lambda: W.periodic_box(16, 8, 4), {}),
+])
+@pytest.mark.parametrize("precision", [W.FP64, W.FP32_STORAGE])
+def test_every_recipe_passes_host_validation(make, kw, precision):
+    """each workload's grid, boundaries, dt/dx and alpha pass rlb_create's
+    checks (stability bounds included): without a device the call gets as
+    far as the device, RLB_E_CUDA"""
+    from paper_1302_1125_gb300 import rlb
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    with pytest.raises(rlb.RLBError) as e:
+        rlb.Grid.from_workload(make(), precision=precision, **kw)
+    assert e.value.status == rlb.RLB_E_CUDA, str(e.value)
