@@ -188,6 +188,7 @@ def test_periodic_box_gamma_bound():
     (lambda: W.tube_8192("b"), {}), (W.cloud_2d, {}), (W.cloud_2d, {"symmetry_2d": 1}),
     (W.cloud_3d, {}), (lambda: W.sphere_cloud("beta02", viscous=True), {}),
     (lambda: W.sphere_cloud("beta09"), {}), (lambda: W.periodic_box(16, 8, 4), {}),
+    (W.cloud_3d, {"model": 1}), (W.tube_800, {"model": 1}),
 ])
 @pytest.mark.parametrize("precision", [W.FP64, W.FP32_STORAGE])
 def test_every_recipe_passes_host_validation(make, kw, precision):
