@@ -72,6 +72,55 @@ def profiled_traffic(summary: str, units: float):
     return float(fields["traffic_bytes_per_cell"].split()[0]) * units
 
 
+def profiled_value(summary: str, key: str):
+    """a per-unit figure (first number after `key:`) from a committed ncu
+    summary, or None if the kernel's sources changed since the capture"""
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+    except OSError:
+        return None
+    keys = ("csrc_sha256:", "csrc_files:", key + ":")
+    fields = dict(ln.split(":", 1) for ln in text.splitlines() if ln.startswith(keys))
+    files = fields.get("csrc_files", "").split() or None
+    if key not in fields or fields.get("csrc_sha256", "").split()[0:1] != [csrc_hash(files)]:
+        return None
+    return float(fields[key].split()[0])
+
+
+# GB300: 152 SMs, 4 warp schedulers each issuing one warp instruction per
+# clock, and an FP64 pipe of 2 lanes per SM (1.26 TFLOP/s of FMA at 2.07 GHz)
+N_SM = 152
+SCHEDULERS_PER_SM = 4
+DP_LANES_PER_SM = 2
+
+
+def alu_roofline(ops_per_unit, units_per_s, lanes_per_clk, clk, what):
+    """achieved / peak of an arithmetic pipe: ops per unit (from the committed
+    profile) x units per second, against lanes per clock x the median SM
+    clock sampled in the timed region"""
+    if ops_per_unit is None or clk is None or not clk.get("sm_mhz"):
+        return None
+    mhz = clk["sm_mhz"]
+    achieved = ops_per_unit * units_per_s / 1e9
+    peak = lanes_per_clk * mhz * 1e6 / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G ops/s", "frac": achieved / peak,
+            "ops_per_unit": ops_per_unit, "sm_mhz": mhz, "what": what}
+
+
+def issue_roofline(instr_per_unit, units_per_s, clk, what):
+    """achieved / peak warp-instruction issue: thread-instructions per unit
+    (the committed profile's warp instructions x 32 / units) / 32 x units
+    per second, against 4 schedulers x 152 SMs x the sampled SM clock"""
+    if instr_per_unit is None or clk is None or not clk.get("sm_mhz"):
+        return None
+    mhz = clk["sm_mhz"]
+    achieved = instr_per_unit / 32.0 * units_per_s / 1e9
+    peak = N_SM * SCHEDULERS_PER_SM * mhz * 1e6 / 1e9
+    return {"bound": "issue", "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+            "frac": achieved / peak, "thread_instructions_per_unit": instr_per_unit, "sm_mhz": mhz,
+            "what": what}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -91,14 +140,21 @@ class ClockSampler:
         self.index = index
         self.proc = None
         self.lines = []
+        self.first = 0
 
     def __enter__(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts once nvidia-smi delivers samples (its
+            # start-up takes longer than a short timed region)
+            t0 = time.perf_counter()
+            while not self.lines and time.perf_counter() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)
+            self.first = len(self.lines)
         except (FileNotFoundError, OSError):
             self.proc = None
         return self
@@ -115,12 +171,22 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        if not self.lines:
+    def mark(self) -> int:
+        """the number of samples so far (a boundary between regions)"""
+        return len(self.lines)
+
+    def summary(self, lo=None, hi=None):
+        """median SM clock and throttle reasons of the samples [lo, hi)
+        (default: from the start of the timed region); a region shorter
+        than the sampling interval gets the sample taken nearest after it"""
+        lo = self.first if lo is None else lo
+        hi = len(self.lines) if hi is None else hi
+        lines = self.lines[lo:hi] or self.lines[hi:hi + 1] or self.lines[-1:]
+        if not lines:
             return None
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 9:
                 continue
@@ -146,11 +212,17 @@ def rejected(clk):
     return clk["sm_max_mhz"] and clk["sm_mhz"] < 0.6 * clk["sm_max_mhz"] and not clk["reasons"]
 
 
-def timed_steps(torch, g, steps, warmup, device_index):
-    """warm up, then time `steps` steps with CUDA events on the launching stream"""
+def timed_steps(torch, g, steps, warmup, device_index, window_s=0.0):
+    """warm up, then time `steps` steps with CUDA events on the launching
+    stream.  With window_s > 0 and a timed region shorter than that, the same
+    steps are repeated afterwards for about window_s seconds (the clock
+    window), timed the same way, so that the clock samples (every 50 ms)
+    cover the kernel running for long enough to mean something; the window
+    is reported beside the timed region, not in its place."""
     g.step(warmup)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
+    window = None
     for attempt in range(2):
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(device_index) as cs:
@@ -162,12 +234,24 @@ def timed_steps(torch, g, steps, warmup, device_index):
             end.record(stream)
             torch.cuda.synchronize()
             barrier()
-        ms = start.elapsed_time(end)
-        launches = g.launches - l0
-        clk = cs.summary()
+            mid = cs.mark()
+            ms = start.elapsed_time(end)
+            launches = g.launches - l0
+            if window_s > 0.0 and ms < 1e3 * window_s:
+                reps = max(1, int(math.ceil(1e3 * window_s / max(ms, 1e-3))))
+                w0, w1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                w0.record(stream)
+                for _ in range(reps):
+                    g.step(steps)
+                w1.record(stream)
+                torch.cuda.synchronize()
+                wms = w0.elapsed_time(w1)
+                window = {"steps": reps * steps, "ms_per_step": wms / (reps * steps),
+                          "clocks": cs.summary(mid, cs.mark())}
+        clk = cs.summary(cs.first, mid)
         if not rejected(clk):
             break
-    return ms, clk, launches
+    return ms, clk, launches, window
 
 
 _dist = None
@@ -254,6 +338,34 @@ def l1_fp32_vs_fp64(torch):
             "n": float(np.abs(a[0] - b[0]).sum() / np.abs(b[0]).sum()),
             "e": float(np.abs(a[1] - b[1]).sum() / np.abs(b[1]).sum()),
             "u_x": float(np.abs(a[2] - b[2]).sum() / np.abs(b[2]).sum())}
+
+
+def l1_cloud_3d(torch, rlb, W, steps=100):
+    """Per-field L1 relative error of the FP32-storage form (both recoveries)
+    against the FP64 form on the headline grid itself, 512 x 256 x 256, after
+    `steps` steps from the same initial state.  The FP64 form matches the
+    FP64 oracle within 1e-10 (tests/test_gpu_parity.py)."""
+    w = W.cloud_3d()
+    fields = [torch.as_tensor(a, device="cuda") for a in w.fields()]
+    out = {}
+    for name, prec, rec in (("fp64", rlb.FP64, 0), ("fp32_storage", rlb.FP32_STORAGE, 0),
+                            ("fp32_storage_rec64", rlb.FP32_STORAGE, 1)):
+        g = rlb.Grid.from_workload(w, precision=prec, recovery_fp64=rec)
+        g.init(*fields).step(steps)
+        out[name] = g.macroscopic(device=False)
+        g.close()
+    del fields
+    ref = out["fp64"]
+    res = {"workload": f"cloud_3d 512x256x256, {steps} steps, against the FP64 form on the same grid",
+           "norm": "sum |a - b| / sum |b| per field; u: the velocity vector, sum |u_a - u_b| / sum |u_b|"}
+    for name in ("fp32_storage", "fp32_storage_rec64"):
+        a = out[name]
+        res[name] = {k: float(np.abs(a[i] - ref[i]).sum() / np.abs(ref[i]).sum())
+                     for i, k in enumerate(("n", "e", "u_x"))}
+        # the velocity as one vector field (u_y, u_z vanish on the symmetry planes)
+        res[name]["u"] = float(np.sqrt(((a[2:5] - ref[2:5]) ** 2).sum(0)).sum() /
+                               np.sqrt((ref[2:5] ** 2).sum(0)).sum())
+    return res
 
 
 def batch_sweep(torch, rlb, W, hbm_peak, device_index):
@@ -350,10 +462,14 @@ def batch_sweep(torch, rlb, W, hbm_peak, device_index):
             "value": value, "unit": UNIT, "ms": ms, "gpu_launches": launches,
             "tuning": {k: v for k, v in t.as_dict().items() if k != "ms"}, "resident_clusters": ncl,
             "autotune_trials": len(trials),
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak,
-                         "note": f"{BYTES_FP32} algorithmic bytes per cell update; the working set of the "
-                                 "tubes in flight is largely L2-resident"},
+            "roofline": issue_roofline(profiled_value("tubes_kernel_batch_512.md",
+                                                      "thread_instructions_per_update"),
+                                       value * 1e6, clk,
+                                       "instruction issue: the tubes in flight are L2-resident (98 % hit "
+                                       "rate), so HBM does not bound the batch; thread-instructions per "
+                                       "cell update from the committed ncu capture"),
+            "hbm_equiv": {"achieved": achieved, "unit": "GB/s", "bytes_per_update": BYTES_FP32,
+                          "note": "algorithmic bytes / time, for comparison with the grid form only"},
             "separate_runs": sep,
             "batched_over_separate_fp64": value / sep["fp64"]["value"],
             "symmetry_1d": reduced,
@@ -575,18 +691,26 @@ def run_ours(args):
     # FP32-storage form (the headline)
     g = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE)
     g.init(*dev_fields)
-    ms, clk, launches = timed_steps(torch, g, args.steps, args.warmup, local)
+    ms, clk, launches, window = timed_steps(torch, g, args.steps, args.warmup, local, window_s=2.0)
     ms = max_over_ranks(torch, ms)
     per_step = ms / args.steps
     value = job_value(world, N * args.steps, ms * 1e-3)
     achieved = BYTES_FP32 * N / (per_step * 1e-3) / 1e9
     g.close()
 
+    # the same form with its Landau-frame recovery in FP64 (recovery_fp64)
+    gr = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE, recovery_fp64=1)
+    gr.init(*dev_fields)
+    msr, clkr, _, _ = timed_steps(torch, gr, args.steps, args.warmup, local)
+    msr = max_over_ranks(torch, msr)
+    value_r = job_value(world, N * args.steps, msr * 1e-3)
+    gr.close()
+
     # FP64 form on the same grid
     g64 = rlb.Grid.from_workload(w, precision=rlb.FP64)
     g64.init(*dev_fields)
     k64 = max(3, args.steps // 10)
-    ms64, _, _ = timed_steps(torch, g64, k64, max(3, args.warmup), local)
+    ms64, clk64, _, _ = timed_steps(torch, g64, k64, max(3, args.warmup), local)
     ms64 = max_over_ranks(torch, ms64)
     value64 = world * N * k64 / (ms64 * 1e-3) / 1e6
     ach64 = BYTES_FP64 * N / (ms64 / k64 * 1e-3) / 1e9
@@ -632,6 +756,7 @@ def run_ours(args):
     cloud2d = cloud_2d_run(torch, rlb, W, hbm_peak) if not args.no_batch else None
     paper = paper_runs(torch, rlb, W) if not args.no_batch and (world == 1 or rank == 0) else None
     basic = basic_model_run(torch, rlb, W, hbm_peak) if not args.no_batch else None
+    l1_headline = l1_cloud_3d(torch, rlb, W) if not args.no_batch else None
     if rank != 0:
         return 0
     l1 = l1_fp32_vs_fp64(torch)
@@ -647,7 +772,11 @@ def run_ours(args):
         "config": {"workload": "cloud_3d: 3-D shock-cloud 512x256x256 (slab-driven shock, pressure "
                                "ratio 10; cloud r=48 at (180,128,128), density x10, pressure balanced); "
                                "eta/s 0.05, alpha 0.2, dt/dx 0.15",
-                   "cells": N, "precision": "FP32 populations and arithmetic, double-float moment sums",
+                   "cells": N,
+                   "precision": "FP32 populations (stored, streamed, relaxed in FP32); moment sums and "
+                                "E^2-|M|^2 in double-float (float pairs, error-free TwoSum/FMA); the rest of "
+                                "the Landau-frame recovery, tau and the equilibrium coefficients in FP32; no FP64 "
+                                "instruction",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                    "l2": "inputs larger than L2: 10.2 GB of populations read+written per step"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
@@ -655,9 +784,26 @@ def run_ours(args):
                      "traffic": profiled_traffic("step_kernel_fp32_cloud_3d.md", N),
                      "note": f"{BYTES_FP32} algorithmic bytes per cell update x {N} cells per launch "
                              f"/ CUDA-event time per launch; peak {peak_kind} copy bandwidth"},
+        "issue": issue_roofline(profiled_value("step_kernel_fp32_cloud_3d.md", "thread_instructions_per_cell"),
+                                value * 1e6 / world, clk,
+                                "instruction issue of the headline kernel; thread-instructions per cell from the "
+                                "committed ncu capture"),
+        "clock_window": window,
+        "fp32_rec64": {"value": value_r, "unit": UNIT, "ms_per_step": msr / args.steps,
+                       "hbm_frac": BYTES_FP32 * N / (msr / args.steps * 1e-3) / 1e9 / hbm_peak,
+                       "precision": "FP32 populations, double-float moment sums, Landau-frame recovery of both "
+                                    "time levels in FP64 (rlb_options.recovery_fp64 = 1)",
+                       "clocks": clkr},
         "fp64_form": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
-                      "hbm_achieved_gbs": ach64, "hbm_frac": ach64 / hbm_peak},
+                      "hbm_achieved_gbs": ach64, "hbm_frac": ach64 / hbm_peak,
+                      "alu": alu_roofline(profiled_value("step_kernel_fp64_cloud_3d.md", "dp_thread_ops_per_cell"),
+                                          value64 * 1e6 / world, N_SM * DP_LANES_PER_SM, clk64,
+                                          "FP64 pipe: DP thread-operations per cell (committed ncu capture) x "
+                                          "cells per second, against 152 SMs x 2 FP64 lanes x the sampled SM "
+                                          "clock"),
+                      "clocks": clk64},
         "fp32_over_fp64": value / value64,
+        "l1_error_headline": l1_headline,
         "l1_error_fp32_vs_fp64": l1,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -132,11 +132,21 @@ typedef struct {
                               * rlb_macroscopic, rlb_conserved_totals and rlb_get_state see
                               * all 19 planes.  Results equal the 19-population step up to the
                               * rounding order of the moment sums. */
+    int recovery_fp64;       /* RLB_FP32_STORAGE only.  1: the Landau-frame recovery of Sec. II (Eq. 38 with
+                              * eps = 3P) of both time levels runs in FP64 arithmetic, from the exact double
+                              * values of the double-float moment sums.  0 (default): E^2 - |M|^2 is formed in
+                              * double-float and the rest of the recovery, well conditioned once E^2 - |M|^2 is
+                              * known, in float.  Both reach the accuracy that the rounding of the stored FP32
+                              * populations allows (relative error of P up to about gamma^2 x 2.6e-7 for
+                              * either); the FP64 form costs FP64 instructions, which GB300 issues at 1/64 of
+                              * the float rate.  Supported with the extended lattice, the viscous step, even nx
+                              * and no symmetry reduction; the threads always take tiles (1-D grids: the 1-D
+                              * form).  rlb_create rejects other combinations with RLB_E_INVALID. */
 } rlb_options;
 
 /* Fill *opts with the defaults: dt/dx 0.25, no overrides, viscous mode, FP64,
  * default stream, no symmetry reduction, the extended lattice, automatic
- * thread mapping. */
+ * thread mapping, double-float recovery (recovery_fp64 = 0). */
 RLB_API void rlb_default_options(rlb_options *opts);
 
 /* Validate a configuration on the host without touching the GPU.  Same
@@ -156,12 +166,18 @@ RLB_API rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over
 /* Create a context for one grid.  eta_over_s sets tau per cell through
  * Eq. 41 with the entropy s = n (4 - ln lambda) of Sec. III (the factor
  * 4 - ln lambda floored at 1e-3); zeta_over_s sets alpha through Eq. 56 at the
- * reference state T = 1, lambda = 1 unless opts->alpha_override >= 0.
+ * reference state T = 1, lambda = 1 (alpha = 27 (zeta/s) / nu^6, 0.0123 zeta/s
+ * on the extended lattice) unless opts->alpha_override >= 0.
  * The step itself (limited-flux streaming, implicit collision) realises a
  * shear viscosity proportional to tau with no -1/2 shift: 0.2369 P tau
  * (extended lattice) or 0.1621 P tau (basic), larger along face diagonals;
  * and the alpha term diffuses momentum with 2.50 alpha (extended) per unit
- * time, adding a viscosity 2.50 alpha (e + P).
+ * time, adding a viscosity 2.50 alpha (e + P).  Eq. 56 does not describe
+ * that term: the sound damping it adds is about 12 times less than the bulk
+ * viscosity 4 P alpha nu^6 / 27 would give.  So zeta/s acts only through
+ * this small alpha: at zeta/s <= 0.1, alpha <= 1.2e-3, far below the
+ * alpha = 0.15 .. 0.2 the paper's runs use for stability.  To set the term
+ * that keeps fast flows physical, give alpha_override. 
  * opts may be NULL (defaults).  Allocates 2 x 38 population planes, 5
  * previous-level planes and scratch on the device; *out receives the handle
  * (NULL on failure).  Errors: RLB_E_INVALID, RLB_E_UNSTABLE, RLB_E_NOMEM,
@@ -266,8 +282,12 @@ RLB_API const char *rlb_status_string(int status);
  * 5 x RLB_NOALLOC_MAX_BLOCKS doubles (47.5 KiB) inside the library, which
  * every GPU that loads the library holds until the process exits.  The
  * first call on a device looks up that array's address on the current
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  All calls on a device share the array: calls whose kernels
+ * device (cudaGetSymbolAddress) and keeps it for the life of the process;
+ * make that first call before any stream capture.  Do not use this entry
+ * point on a device after cudaDeviceReset in the same process: the reset
+ * unloads the library's device code, the array may come back at another
+ * address, and the kept address would then be stale.  All calls on a device
+ * share the array: calls whose kernels
  * overlap on the GPU (different streams, no ordering between them) race and
  * give wrong totals.  Nothing in the array needs clearing between calls;
  * every slot a call reads it has written first.  Calls no cudaMalloc,
@@ -322,7 +342,7 @@ typedef struct {
  * through Eq. 56 per tube, as in rlb_create; opts->alpha_override >= 0 sets
  * one alpha for all tubes).  opts may be NULL: defaults of
  * rlb_default_options with precision RLB_FP32_STORAGE.  Requirements:
- * precision RLB_FP32_STORAGE, euler_mode 0, model 0, symmetry_1d 0 or 1 (the
+ * precision RLB_FP32_STORAGE, euler_mode 0, model 0, recovery_fp64 0, symmetry_1d 0 or 1 (the
  * tubes are 1-D with u_y = u_z = 0, so the reduction is exact; thread_mapping
  * and symmetry_2d do not apply to tubes and are ignored), at most 2^30 stored cells
  * (each tube stored from a 128-byte boundary).  RLB_E_UNSTABLE if

@@ -145,6 +145,16 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
         if ((g.bc_lo[0] == RLB_BC_INLET || g.bc_hi[0] == RLB_BC_INLET) && g.inlet_u[2] != 0.0)
             return fail(ctx, RLB_E_INVALID, "symmetry_2d needs inlet_u[2] = 0");
     }
+    if (o.recovery_fp64 != 0 && o.recovery_fp64 != 1) return fail(ctx, RLB_E_INVALID, "recovery_fp64 must be 0 or 1");
+    if (o.recovery_fp64) {
+        if (o.precision != RLB_FP32_STORAGE)
+            return fail(ctx, RLB_E_INVALID, "recovery_fp64 is an option of the FP32-storage form");
+        if (o.euler_mode != 0 || o.model != 0 || o.symmetry_1d || o.symmetry_2d || o.thread_mapping == 2 ||
+            g.nx % 2 != 0)
+            return fail(ctx, RLB_E_INVALID,
+                        "recovery_fp64 needs the extended lattice, the viscous step, even nx, no symmetry "
+                        "reduction and tiles");
+    }
     if (!std::isfinite(o.tau_override) || !std::isfinite(o.alpha_override))
         return fail(ctx, RLB_E_INVALID, "overrides must be finite");
     // explicit stability bounds
@@ -237,6 +247,7 @@ void rlb_default_options(rlb_options *o)
     o->model = 0;
     o->thread_mapping = 0;
     o->symmetry_2d = 0;
+    o->recovery_fp64 = 0;
 }
 
 rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
@@ -396,7 +407,11 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
     for (long long k = 0; k < nsteps; ++k) {
         const int c = ctx->cur, o = 1 - c;
         cudaError_t e;
-        if (ctx->fp32)
+        if (ctx->fp32 && ctx->opt.recovery_fp64)
+            e = rlb::launch_step_f32_rec64(ctx->sp, ctx->dim, (const float *)ctx->fbuf[c],
+                                           (const float *)ctx->hbuf[c], (float *)ctx->fbuf[o],
+                                           (float *)ctx->hbuf[o], (float *)ctx->prev, ctx->stream);
+        else if (ctx->fp32)
             e = rlb::launch_step_f32(ctx->sp, ctx->dim, ctx->opt.euler_mode, (const float *)ctx->fbuf[c],
                                      (const float *)ctx->hbuf[c], (float *)ctx->fbuf[o], (float *)ctx->hbuf[o],
                                      (float *)ctx->prev, ctx->stream);

@@ -378,6 +378,8 @@ rlb_status rlb_batch_create(int B, const int *nx, const double *eta_over_s, cons
     if (o.euler_mode != 0) return bfail(nullptr, RLB_E_INVALID, "the batched path runs the viscous step only");
     if (o.symmetry_1d != 0 && o.symmetry_1d != 1) return bfail(nullptr, RLB_E_INVALID, "symmetry_1d must be 0 or 1");
     if (o.model != 0) return bfail(nullptr, RLB_E_INVALID, "the batched path runs the extended lattice (model 0)");
+    if (o.recovery_fp64 != 0)
+        return bfail(nullptr, RLB_E_INVALID, "the batched path runs the double-float recovery (recovery_fp64 = 0)");
     if (limiter != RLB_LIMITER_MINMOD && limiter != RLB_LIMITER_NONE)
         return bfail(nullptr, RLB_E_INVALID, "unknown limiter");
     if (!(o.dt_over_dx > 0.0) || !std::isfinite(o.dt_over_dx))

@@ -35,6 +35,9 @@ cudaError_t launch_step_f64(const StepParams &p, int dim, int euler, const doubl
                             double *fo, double *ho, double *prev, cudaStream_t s);
 cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f, const float *h,
                             float *fo, float *ho, float *prev, cudaStream_t s);
+// the FP32-storage step with the FP64 recovery (rlb_options.recovery_fp64)
+cudaError_t launch_step_f32_rec64(const StepParams &p, int dim, const float *f, const float *h, float *fo,
+                                  float *ho, float *prev, cudaStream_t s);
 
 cudaError_t launch_init(int fp32, int N, long long ps, const double *n, const double *T,
                         const double *ux, const double *uy, const double *uz, void *f, void *h,

@@ -27,7 +27,9 @@ std::mutex g_mu;
 double *g_partial_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on the current device, looked up once
-// per device.  The name g_partial is only a host-side stand-in in host code.
+// per device and kept for the life of the process (the header states that a
+// cudaDeviceReset invalidates it).  The name g_partial is only a host-side
+// stand-in in host code.
 cudaError_t scratch_for_current_device(double **out)
 {
     int dev = 0;

@@ -5,8 +5,12 @@
 // T^00 and T^0a are accumulated error-free as double-float pairs (TwoSum),
 // and E^2 - |M|^2, the quantity whose cancellation grows like gamma^2 in the
 // Landau-frame recovery, is formed in double-float before one rounding; the
-// rest of the recovery, tau and the equilibrium coefficients are FP32.  No
-// FP64 instruction is issued.
+// rest of the recovery (a well-conditioned function of E^2 - |M|^2, E, M and
+// N^0), tau and the equilibrium coefficients are FP32.  No FP64 instruction
+// is issued.  The previous level's recovery is the same arithmetic on its
+// stored float sums.  The REC64 variant (rlb_options.recovery_fp64) runs
+// both recoveries in FP64 from the exact double values of the sums instead;
+// it exists to measure what FP64 buys over the double-float form.
 //
 // Conservation: the float equilibrium coefficients carry fixed roundings of
 // irrational constants (weights, 4/xi0, 13/9, ...) that would bias their
@@ -358,28 +362,32 @@ __device__ __forceinline__ Mac2 recover2(const df2 &S, const df2 &Vx, const df2 
     return m;
 }
 
-// the same recovery from plain float sums (used for the previous level, whose
-// equilibrium only shapes the non-conserved part of 2 f^eq(t) - f^eq(t - dt))
+// The same recovery in FP64 (REC64 step variant): the double-float sums are
+// converted to double exactly (hi + lo), the Landau-frame recovery runs in
+// double arithmetic (rlb_device.cuh: recover, IEEE division and square root)
+// and its results are rounded once to float for the equilibrium coefficients.
 template <int LAT>
-__device__ __forceinline__ Mac2 recover2f(f2 S, f2 Vx, f2 Vy, f2 Vz, f2 Sh)
+__device__ __forceinline__ Mac2 recover2_64(const df2 &S, const df2 &Vx, const df2 &Vy, const df2 &Vz,
+                                            const df2 &Hs, bool &ok0, bool &ok1)
 {
-    constexpr float kXi0 = float(Lat<LAT>::xi0), kXi0Sq = float(Lat<LAT>::xi0sq);
-    const f2 E = bc(kXi0Sq) * S;
-    const f2 M2 = bc(kXi0Sq) * fma2(Vx, Vx, fma2(Vy, Vy, Vz * Vz));
-    const f2 D = fma2(E, E, -M2);
-    const f2 root2 = fma2(E, E, bc(3.0f) * D);
-    const f2 den = E + f2{sqrtf(root2.x), sqrtf(root2.y)};
+    constexpr double xi0 = Lat<LAT>::xi0, xi0sq = Lat<LAT>::xi0sq;
+    auto dd = [](float hi, float lo) { return double(hi) + double(lo); };
+    Macro a, b;
+    ok0 = recover(xi0sq * dd(S.hi.x, S.lo.x), xi0 * dd(Vx.hi.x, Vx.lo.x), xi0 * dd(Vy.hi.x, Vy.lo.x),
+                  xi0 * dd(Vz.hi.x, Vz.lo.x), xi0 * dd(Hs.hi.x, Hs.lo.x), a);
+    ok1 = recover(xi0sq * dd(S.hi.y, S.lo.y), xi0 * dd(Vx.hi.y, Vx.lo.y), xi0 * dd(Vy.hi.y, Vy.lo.y),
+                  xi0 * dd(Vz.hi.y, Vz.lo.y), xi0 * dd(Hs.hi.y, Hs.lo.y), b);
     Mac2 m;
-    m.P = f2{fdiv(D.x, den.x), fdiv(D.y, den.y)};
-    const f2 fourP = bc(4.0f) * m.P;
-    const f2 g = f2{sqrtf(fdiv(E.x + m.P.x, fourP.x)), sqrtf(fdiv(E.y + m.P.y, fourP.y))};
-    const f2 s = f2{fdiv(kXi0, fourP.x * g.x), fdiv(kXi0, fourP.y * g.y)};
-    m.ux = Vx * s;
-    m.uy = Vy * s;
-    m.uz = Vz * s;
-    m.n = f2{fdiv(kXi0 * Sh.x, g.x), fdiv(kXi0 * Sh.y, g.y)};
+    m.P = f2{float(a.P), float(b.P)};
+    m.ux = f2{float(a.ux), float(b.ux)};
+    m.uy = f2{float(a.uy), float(b.uy)};
+    m.uz = f2{float(a.uz), float(b.uz)};
+    m.n = f2{float(a.n), float(b.n)};
     return m;
 }
+
+// a float sum as a double-float with zero low part
+__device__ __forceinline__ df2 as_df2(f2 v) { return df2{v, bc(0.0f)}; }
 
 // tau from eta/s (Eq. 41 with the entropy of Sec. III), float
 template <int LAT>
@@ -546,7 +554,7 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
 // previous level's planes of the zero sums (sum c_z f; 1-D also sum c_y f)
 // are left alone.
 template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false, int NP = 19,
-          int LAT = 0>
+          int LAT = 0, bool REC64 = false>
 __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
                                             const float *__restrict__ f, const float *__restrict__ h,
                                             float *__restrict__ fo, float *__restrict__ ho,
@@ -558,6 +566,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
     static_assert(!STAGE || (VEC2 && !EULER), "staging needs aligned pairs and the viscous step");
     static_assert(NP == 19 || (NP == 7 && DIM == 1 && !EULER) || (NP == 14 && DIM == 2 && !EULER),
                   "the symmetry reductions are 1-D or 2-D and viscous");
+    static_assert(!REC64 || (!EULER && NP == 19), "the FP64 recovery is a variant of the viscous 19-population step");
     constexpr int NI = 2 * NP;   // items: f classes, then h classes
     unsigned sdst0 = 0;
     if constexpr (STAGE) {
@@ -612,7 +621,9 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         });
         const f2 Sh = Hs.hi + Hs.lo;
         bool ok0, ok1;
-        const Mac2 mt = recover2<LAT>(S, Vx, Vy, Vz, Sh, ok0, ok1);
+        Mac2 mt;
+        if constexpr (REC64) mt = recover2_64<LAT>(S, Vx, Vy, Vz, Hs, ok0, ok1);
+        else mt = recover2<LAT>(S, Vx, Vy, Vz, Sh, ok0, ok1);
         if (!ok0 || (g.has1 && !ok1)) atomicOr(p.status, unsigned(ST_NONPHYSICAL));
 
         f2 kap;
@@ -636,7 +647,20 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         const f2 Vpy = has_vy<NP>() ? ldpair<VEC2, LD>(prev + 2 * ps, g, 0) : bc(0.0f);
         const f2 Vpz = has_vz<NP>() ? ldpair<VEC2, LD>(prev + 3 * ps, g, 0) : bc(0.0f);
         const f2 Shp = ldpair<VEC2, LD>(prev + 4 * ps, g, 0);
-        const Mac2 mp = recover2f<LAT>(Sp, Vpx, Vpy, Vpz, Shp);
+        // the previous level's recovery: the same arithmetic as this level's,
+        // from its stored float sums.  Its validity is not checked again: the
+        // same sums passed the check as the current level one step earlier
+        // (or in rlb_init), and the flags' registers cost spills here.
+        Mac2 mp;
+        {
+            bool okp0, okp1;
+            if constexpr (REC64)
+                mp = recover2_64<LAT>(as_df2(Sp), as_df2(Vpx), as_df2(Vpy), as_df2(Vpz), as_df2(Shp), okp0, okp1);
+            else
+                mp = recover2<LAT>(as_df2(Sp), as_df2(Vpx), as_df2(Vpy), as_df2(Vpz), Shp, okp0, okp1);
+            (void)okp0;
+            (void)okp1;
+        }
         const f2 T0 = fma2(bc(2.0f), S.hi + S.lo, -Sp);
         f2 Ta[3];
         Ta[0] = fma2(bc(2.0f), Vx.hi + Vx.lo, -Vpx);
@@ -777,7 +801,7 @@ constexpr size_t step_smem_bytes(int nthr, bool stage, int dim)
 // order (rows of ceil(nx / 2) pairs), for grids whose nx does not fill the
 // tiles; otherwise blocks of 32 x BY threads take tiles of 64 x BY cells in
 // one z-plane (the 1-D form: one row of tiles)
-template <int DIM, bool EULER, bool VEC2, int LAT, int NP = 19, bool LIN = false>
+template <int DIM, bool EULER, bool VEC2, int LAT, int NP = 19, bool LIN = false, bool REC64 = false>
 __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
     step_f32_kernel(const StepParams p, const float *__restrict__ f, const float *__restrict__ h,
                     float *__restrict__ fo, float *__restrict__ ho, float *__restrict__ prev)
@@ -830,7 +854,7 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
     const int nthr = blockDim.x * blockDim.y;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     constexpr bool STAGE = kStageOn && VEC2 && !EULER;
-    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE, NP, LAT>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho,
+    update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE, NP, LAT, REC64>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho,
                                                                   prev, ps,
                                                          s_park + tid, nthr,
                                                          s_park + (kParkOn ? kParkSlots * nthr : 0) + tid, nthr);

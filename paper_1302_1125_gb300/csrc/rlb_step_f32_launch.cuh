@@ -22,14 +22,14 @@ inline bool f32_use_linear(const StepParams &p, int dim)
     return fill < 0.97;
 }
 
-template <int DIM, bool EULER, bool VEC2, int LAT, int NP, bool LIN>
+template <int DIM, bool EULER, bool VEC2, int LAT, int NP, bool LIN, bool REC64 = false>
 cudaError_t launch_f32(const StepParams &p, const float *f, const float *h, float *fo, float *ho, float *prev,
                        cudaStream_t s)
 {
-    if constexpr (DIM == 2 && !EULER && NP == 19) {
+    if constexpr (DIM == 2 && !EULER && NP == 19 && !REC64) {
         if (p.sym == 2) return launch_f32<2, false, VEC2, LAT, 14, LIN>(p, f, h, fo, ho, prev, s);
     }
-    if constexpr (DIM == 1 && !EULER && NP == 19 && !LIN) {
+    if constexpr (DIM == 1 && !EULER && NP == 19 && !LIN && !REC64) {
         if (p.sym == 1) return launch_f32<1, false, VEC2, LAT, 7, false>(p, f, h, fo, ho, prev, s);
     }
     const int npairs = (p.nx + 1) / 2;
@@ -58,12 +58,12 @@ cudaError_t launch_f32(const StepParams &p, const float *f, const float *h, floa
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= kMaxDevices || !attr_set[dev].load(std::memory_order_acquire)) {
-        e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2, LAT, NP, LIN>,
+        e = cudaFuncSetAttribute(f32::step_f32_kernel<DIM, EULER, VEC2, LAT, NP, LIN, REC64>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         if (e != cudaSuccess) return e;
         if (dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
     }
-    f32::step_f32_kernel<DIM, EULER, VEC2, LAT, NP, LIN><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev);
+    f32::step_f32_kernel<DIM, EULER, VEC2, LAT, NP, LIN, REC64><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev);
     return cudaGetLastError();
 }
 

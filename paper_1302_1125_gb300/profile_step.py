@@ -66,7 +66,8 @@ def arg_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="cloud_3d", choices=sorted(MAKERS))
     ap.add_argument("--scale", type=int, default=1)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp32_rec64", "fp64"],
+                    help="fp32_rec64: FP32 storage with the FP64 recovery (recovery_fp64 = 1)")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--tuning", default="", help="batch launch shape threads,bound,cluster,pairs_per_thread")
@@ -80,8 +81,8 @@ def main():
     if a.workload == "batch_tubes":
         return run_batch(a)
     w = MAKERS[a.workload](a.scale)
-    prec = rlb.FP32_STORAGE if a.precision == "fp32" else rlb.FP64
-    g = rlb.Grid.from_workload(w, precision=prec)
+    prec = rlb.FP64 if a.precision == "fp64" else rlb.FP32_STORAGE
+    g = rlb.Grid.from_workload(w, precision=prec, recovery_fp64=int(a.precision == "fp32_rec64"))
     g.init(*[torch.as_tensor(x, device="cuda") for x in w.fields()])
     g.step(a.warmup)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

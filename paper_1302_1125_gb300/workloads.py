@@ -279,6 +279,56 @@ def periodic_box(nx, ny=1, nz=1, *, seed=7, amp=0.2, gamma_max=3.0, dt_over_dx=0
                     make_fields=lambda: tuple(a.copy() for a in fl))
 
 
+def boosted_box(nx, ny=1, nz=1, *, gamma=10.0, direction=(1.0, 0.0, 0.0), amp=1e-3, dt_over_dx=0.15,
+                tau_override=1.0, alpha_override=0.2, precision=FP32_STORAGE, steps=2000,
+                name="boosted_box") -> Workload:
+    """Periodic box of gas at T = 1, n = n_eq(1) moving as a whole at Lorentz
+    factor `gamma` along `direction` (normalised here), with a small
+    temperature and density ripple of relative size `amp` that varies along
+    x only (amp = 0: a uniform boosted state).  The states of the
+    high-gamma precision checks: the regime, gamma ~ 10, where the
+    Landau-frame recovery meets the 1 - beta^2 cancellation."""
+    d = np.asarray(direction, np.float64)
+    d = d / np.linalg.norm(d)
+    beta = math.sqrt(1.0 - 1.0 / gamma ** 2)
+    x = np.arange(nx, dtype=np.float64)
+    ripple = np.cos(2 * math.pi * x / nx + 0.3) + 0.5 * np.sin(4 * math.pi * x / nx + 1.1)
+    T1 = 1.0 + amp * ripple
+    n1 = float(n_eq(1.0)) * (1.0 + 0.5 * amp * np.cos(2 * math.pi * x / nx + 2.0))
+
+    def col(v):
+        return np.ascontiguousarray(np.broadcast_to(v, (nz, ny, nx)).reshape(-1), np.float64)
+    fl = [col(n1), col(T1)] + [col(np.full(nx, beta * d[a])) for a in range(3)]
+    per = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
+    return Workload(name, nx, ny, nz, per, per, dt_over_dx, 0.05, 0.0, steps, precision,
+                    tau_override=tau_override, alpha_override=alpha_override,
+                    make_fields=lambda: tuple(a.copy() for a in fl))
+
+
+def smooth_gamma_box(nx, ny, nz, *, gamma_max=15.0, seed=11, ripple=0.0, dt_over_dx=0.15, tau_override=1.0,
+                     alpha_override=0.2, precision=FP32_STORAGE, name="smooth_gamma_box") -> Workload:
+    """Periodic box whose Lorentz factor rises smoothly along x from 1 to
+    gamma_max and back (a raised cosine), moving in a direction that turns
+    slowly along x, with seeded ripples of relative size `ripple` in T and n
+    across y and z: a state spanning gamma 1 .. gamma_max for cell-by-cell
+    checks of single steps."""
+    rng = np.random.default_rng(seed)
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    g = 1.0 + (gamma_max - 1.0) * 0.5 * (1.0 - np.cos(2 * math.pi * xx / nx))
+    beta = np.sqrt(1.0 - 1.0 / g ** 2)
+    ph = rng.uniform(0, 2 * math.pi, 4)
+    th = 0.5 * np.sin(2 * math.pi * xx / nx + ph[0])
+    ps = 0.3 * np.cos(2 * math.pi * xx / nx + ph[1])
+    d = [np.cos(th) * np.cos(ps), np.sin(th) * np.cos(ps), np.sin(ps)]
+    T = 1.0 + ripple * np.cos(2 * math.pi * (yy / max(ny, 1) + zz / max(nz, 1)) + ph[2])
+    n = n_eq(T) * (1.0 + ripple * np.sin(2 * math.pi * (zz / max(nz, 1) - yy / max(ny, 1)) + ph[3]))
+    fl = [np.ascontiguousarray(a.reshape(-1), np.float64) for a in (n, T, *(beta * c for c in d))]
+    per = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
+    return Workload(name, nx, ny, nz, per, per, dt_over_dx, 0.05, 0.0, 1, precision,
+                    tau_override=tau_override, alpha_override=alpha_override,
+                    make_fields=lambda: tuple(a.copy() for a in fl))
+
+
 def sphere_cloud(case="beta09", scale=1, *, viscous=False, precision=FP32_STORAGE, steps=None) -> Workload:
     """The paper's 3-D shock-cloud run with a solid sphere (Sec. III), every
     length divided by `scale` (steps too, so the same physical time)."""

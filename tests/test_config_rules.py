@@ -6,6 +6,9 @@ configurations (CPU, no device):
   with n <= 0, T <= 0, |u| >= 1; eta/s or zeta/s negative or not finite;
   dt/dx not positive and finite; non-finite overrides; a symmetry reduction
   on a grid or inlet it does not fit, with Euler mode, or both at once;
+  recovery_fp64 other than 0 or 1, or 1 without FP32 storage, with Euler
+  mode, the basic lattice, a symmetry reduction, the linear mapping or odd
+  nx;
 * else RLB_E_UNSTABLE when dt/dx times the largest sum over moving axes of
   |c_ia| c0/c_t exceeds 1, or 2 d (c0 nu/c_t) dt alpha exceeds 1, with d the
   number of axes with more than one cell (at least 1) and alpha the override
@@ -49,6 +52,10 @@ def expected(nx, ny, nz, lo, hi, inlet_n, inlet_T, inlet_u, eta, zeta, limiter, 
     if o["sym2"] == 1:
         invalid |= o["euler"] != 0 or nz != 1 or ny < 2 or (has_inlet and inlet_u[2] != 0)
     invalid |= o["sym1"] == 1 and o["sym2"] == 1
+    invalid |= o["rec64"] not in (0, 1)
+    if o["rec64"] == 1:
+        invalid |= (o["precision"] != 1 or o["euler"] != 0 or o["model"] != 0 or o["sym1"] != 0
+                    or o["sym2"] != 0 or o["mapping"] == 2 or nx % 2 != 0)
     invalid |= not (math.isfinite(o["tau"]) and math.isfinite(o["alpha"]))
     if invalid:
         return rlb.RLB_E_INVALID
@@ -78,15 +85,16 @@ vel = st.sampled_from([0.0, 0.3, -0.6, 0.9, 1.0])
            sym1=st.sampled_from([0, 1, 2]), sym2=st.sampled_from([0, 1, 2]),
            model=st.sampled_from([0, 1, 2]), mapping=st.sampled_from([-1, 0, 1, 2, 3]),
            tau=st.sampled_from([0.0, 0.8, math.inf]),
-           alpha=st.sampled_from([-1.0, 0.0, 0.05, 0.2, 0.5, math.nan]))
+           alpha=st.sampled_from([-1.0, 0.0, 0.05, 0.2, 0.5, math.nan]),
+           rec64=st.sampled_from([0, 0, 1, 1, 2]))
 def test_check_config_follows_the_documented_rules(nx, ny, nz, lo, hi, inlet_n, inlet_T, inlet_u, eta,
                                                    zeta, limiter, dt, precision, euler, sym1, sym2,
-                                                   model, mapping, tau, alpha):
+                                                   model, mapping, tau, alpha, rec64):
     o = dict(dt=dt, precision=precision, euler=euler, sym1=sym1, sym2=sym2, model=model,
-             mapping=mapping, tau=tau, alpha=alpha)
+             mapping=mapping, tau=tau, alpha=alpha, rec64=rec64)
     g = rlb.make_grid(nx, ny, nz, lo, hi, (inlet_n, inlet_T, inlet_u))
     opts = rlb.make_options(dt, tau, alpha, euler, precision, None, symmetry_1d=sym1, model=model,
-                            thread_mapping=mapping, symmetry_2d=sym2)
+                            thread_mapping=mapping, symmetry_2d=sym2, recovery_fp64=rec64)
     got = rlb.rlb_check_config(g, 19, eta, zeta, limiter, opts)
     assert got == expected(nx, ny, nz, lo, hi, inlet_n, inlet_T, inlet_u, eta, zeta, limiter, o)
 
@@ -117,6 +125,7 @@ def batch_expected(nx, eta, zeta, limiter, o):
     B = len(nx)
     invalid = not (1 <= B <= 65535)
     invalid |= o["precision"] != 1 or o["euler"] != 0 or o["sym1"] not in (0, 1) or o["model"] != 0
+    invalid |= o.get("rec64", 0) != 0
     invalid |= limiter not in (0, 1)
     invalid |= not (o["dt"] > 0 and math.isfinite(o["dt"]))
     invalid |= not (math.isfinite(o["tau"]) and math.isfinite(o["alpha"]))

@@ -202,3 +202,35 @@ def test_every_recipe_passes_host_validation(make, kw, precision):
     with pytest.raises(rlb.RLBError) as e:
         rlb.Grid.from_workload(make(), precision=precision, **kw)
     assert e.value.status == rlb.RLB_E_CUDA, str(e.value)
+
+
+@pytest.mark.parametrize("gamma,direction,amp", [(10.0, (1.0, 0.0, 0.0), 1e-3), (20.0, (1.0, 1.0, 1.0), 0.0),
+                                                 (5.0, (0.0, 2.0, 1.0), 1e-2)])
+def test_boosted_box(gamma, direction, amp):
+    w = W.boosted_box(16, 4, 2, gamma=gamma, direction=direction, amp=amp)
+    assert w.bc_lo == w.bc_hi == (W.BC_PERIODIC,) * 3
+    n, T, ux, uy, uz = (grid(w, a) for a in w.fields())
+    v2 = ux ** 2 + uy ** 2 + uz ** 2
+    assert np.allclose(1.0 / np.sqrt(1.0 - v2), gamma, rtol=1e-12)
+    d = np.asarray(direction) / np.linalg.norm(direction)
+    for a, c in zip((ux, uy, uz), d):
+        assert np.allclose(a / np.sqrt(v2), c, atol=1e-15)
+    # the ripple: relative size amp in T (amp / 2 in n) and along x only
+    assert np.abs(T - 1.0).max() <= 1.5 * amp + 1e-15
+    assert np.abs(n / W.n_eq(1.0) - 1.0).max() <= 0.5 * amp + 1e-15
+    for a in (n, T):
+        assert np.array_equal(a, np.broadcast_to(a[:1, :1, :], a.shape))
+    if amp == 0.0:
+        assert np.all(T == 1.0) and np.all(n == W.n_eq(1.0))
+
+
+def test_smooth_gamma_box_spans_the_range():
+    w = W.smooth_gamma_box(128, 8, 4, gamma_max=15.0)
+    n, T, ux, uy, uz = (grid(w, a) for a in w.fields())
+    gam = 1.0 / np.sqrt(1.0 - (ux ** 2 + uy ** 2 + uz ** 2))
+    assert gam.min() == pytest.approx(1.0, abs=1e-12)
+    assert gam.max() == pytest.approx(15.0, rel=2e-3)
+    assert np.all(n > 0) and np.all(T > 0)
+    # every field varies along x only (no gradient across the flow)
+    for a in (n, T, ux, uy, uz, gam):
+        assert np.array_equal(a, np.broadcast_to(a[:1, :1, :], a.shape))
