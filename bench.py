@@ -793,6 +793,11 @@ def run_ours(args):
                        "hbm_frac": BYTES_FP32 * N / (msr / args.steps * 1e-3) / 1e9 / hbm_peak,
                        "precision": "FP32 populations, double-float moment sums, Landau-frame recovery of both "
                                     "time levels in FP64 (rlb_options.recovery_fp64 = 1)",
+                       "alu": alu_roofline(profiled_value("step_kernel_fp32_rec64_cloud_3d.md", "dp_thread_ops_per_cell"),
+                                           value_r * 1e6 / world, N_SM * DP_LANES_PER_SM, clkr,
+                                           "FP64 pipe: the recovery's DP thread-operations per cell (committed ncu "
+                                           "capture) x cells per second, against 152 SMs x 2 FP64 lanes x the "
+                                           "sampled SM clock"),
                        "clocks": clkr},
         "fp64_form": {"value": value64, "unit": UNIT, "steps": k64, "ms_per_step": ms64 / k64,
                       "hbm_achieved_gbs": ach64, "hbm_frac": ach64 / hbm_peak,
