@@ -118,8 +118,13 @@ typedef struct {
                               * of two x-adjacent cells each, 64 x 8 cells; FP64: 32 x 4 cells),
                               * the better reuse of y-neighbours in L1; 2: linear, one block per
                               * run of consecutive cells (pairs) of the x-fastest order, no idle
-                              * lanes whatever nx and ny.  The results are the same bit for
-                              * bit. */
+                              * lanes whatever nx and ny; 3: tiles, and in the FP32-storage form
+                              * on grids that allow it (3-D, viscous, extended lattice, nx a
+                              * multiple of 64, ny of 8, x faces not periodic) the block stages
+                              * each population's stencil tile into shared memory by bulk copies
+                              * instead of each thread staging its own (see rlb_step_kernel;
+                              * measured slower on the 512 x 256 x 256 cloud, so not the
+                              * default).  The results are the same bit for bit. */
     int symmetry_2d;         /* 1 (grids with nz = 1 < ny, either precision, viscous step): exact 2-D
                               * symmetry reduction.  With u_z = 0 in every cell (and at the
                               * inlet) the state is its own mirror image in z, so mirror-image
@@ -264,6 +269,18 @@ RLB_API const char *rlb_last_error(const rlb_ctx *ctx);
 
 /* Name of a status code. */
 RLB_API const char *rlb_status_string(int status);
+
+/* Name of the step kernel rlb_step launches for this context (a
+ * diagnostic; the paper has no counterpart): "fp32_bulk_tiles" (FP32
+ * storage on 3-D grids whose stencil tiles are staged by block-wide bulk
+ * copies: thread_mapping 3, viscous step, extended lattice, nx a multiple
+ * of 64, ny of 8, x faces not periodic), "fp32_tiles" (tiles of
+ * 64 x 8 cells, each thread loading its own stencil, staged by asynchronous
+ * copies in the viscous step), "fp32_linear", "fp32_1d", "fp32_rec64" (recovery_fp64),
+ * "fp64_tiles", "fp64_linear", "fp64_small" (blocks of one to four warps
+ * on grids with fewer cells than one block per SM), "fp64_1d".  The
+ * results are the same whichever kernel runs.  NULL ctx: "none". */
+RLB_API const char *rlb_step_kernel(const rlb_ctx *ctx);
 
 /* Grid totals without any allocation.  The paper has no counterpart: this
  * serves callers that cannot call cudaMalloc, for example an application

@@ -16,6 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "librlb.so")
 BUILD = os.path.join(HERE, "_build")
 SOURCES = ["rlb_api.cu", "rlb_aux.cu", "rlb_step_f64.cu", "rlb_step_f32.cu", "rlb_step_f32_lin.cu", "rlb_step_f32_rec64.cu",
+           "rlb_step_f32_bulk.cu",
            "rlb_noalloc.cu",
            "rlb_batch_api.cpp", "rlb_batch_aux.cu", "rlb_batch_ca.cu", "rlb_batch_cg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -40,6 +40,8 @@ struct rlb_ctx {
     cudaStream_t stream;
     long long launches;
     StepParams sp;
+    rlb::TileMaps tmaps[2];   // tensor maps of the population buffers (bulk-staged FP32 tiles)
+    bool have_tmaps = false;
     bool sym_stale = false;   // symmetry reduction: the non-representative class planes are not yet refreshed
     std::string err;
 };
@@ -134,8 +136,9 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
             return fail(ctx, RLB_E_INVALID, "symmetry_1d needs inlet_u[1] = inlet_u[2] = 0");
     }
     if (o.model != 0 && o.model != 1) return fail(ctx, RLB_E_INVALID, "model must be 0 (extended) or 1 (basic)");
-    if (o.thread_mapping < 0 || o.thread_mapping > 2)
-        return fail(ctx, RLB_E_INVALID, "thread_mapping must be 0 (automatic), 1 (tiles) or 2 (linear)");
+    if (o.thread_mapping < 0 || o.thread_mapping > 3)
+        return fail(ctx, RLB_E_INVALID,
+                    "thread_mapping must be 0 (automatic), 1 (tiles), 2 (linear) or 3 (tiles, bulk-staged)");
     if (o.symmetry_2d != 0 && o.symmetry_2d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_2d must be 0 or 1");
     if (o.symmetry_1d && o.symmetry_2d) return fail(ctx, RLB_E_INVALID, "symmetry_1d and symmetry_2d exclude each other");
     if (o.symmetry_2d) {
@@ -202,6 +205,10 @@ rlb_status check_device_status(rlb_ctx *ctx, rlb_status if_bad)
     if (st != 0u) {
         RLB_CUDA(ctx, cudaMemsetAsync(ctx->d_status, 0, sizeof(unsigned), ctx->stream));
         RLB_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        if (st & rlb::ST_TIMEOUT)
+            return fail(ctx, RLB_E_TIMEOUT,
+                        "a bounded wait of the step kernel gave up (a bulk copy of the stencil tiles did not "
+                        "complete); the results of that step are not valid");
         if (st & rlb::ST_ASYMMETRIC)
             return fail(ctx, RLB_E_INVALID,
                         "symmetry reduction: the state is not its own mirror image (u_y or u_z != 0, or unequal "
@@ -364,6 +371,14 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
         sp.f_ghost_f[i] = float(sp.ghost_f[i]);
         sp.f_ghost_h[i] = float(sp.ghost_h[i]);
     }
+    // the bulk-staged FP32 tiles copy the centre rows and z-neighbour planes
+    // as tensor-map boxes; without the maps they copy row by row
+    if (ctx->fp32 && !o.recovery_fp64 && rlb::f32_bulk_eligible(sp, ctx->dim, o.euler_mode)) {
+        ctx->have_tmaps = rlb::make_tile_maps(sp, (const float *)ctx->fbuf[0], (const float *)ctx->hbuf[0],
+                                              &ctx->tmaps[0]) == cudaSuccess &&
+                          rlb::make_tile_maps(sp, (const float *)ctx->fbuf[1], (const float *)ctx->hbuf[1],
+                                              &ctx->tmaps[1]) == cudaSuccess;
+    }
     ctx->cur = 0;
     ctx->err = "no error";
     *out = ctx;
@@ -414,7 +429,7 @@ rlb_status rlb_step(rlb_ctx *ctx, long long nsteps)
         else if (ctx->fp32)
             e = rlb::launch_step_f32(ctx->sp, ctx->dim, ctx->opt.euler_mode, (const float *)ctx->fbuf[c],
                                      (const float *)ctx->hbuf[c], (float *)ctx->fbuf[o], (float *)ctx->hbuf[o],
-                                     (float *)ctx->prev, ctx->stream);
+                                     (float *)ctx->prev, ctx->stream, ctx->have_tmaps ? &ctx->tmaps[c] : nullptr);
         else
             e = rlb::launch_step_f64(ctx->sp, ctx->dim, ctx->opt.euler_mode, (const double *)ctx->fbuf[c],
                                      (const double *)ctx->hbuf[c], (double *)ctx->fbuf[o],
@@ -585,6 +600,16 @@ void rlb_destroy(rlb_ctx *ctx)
 const char *rlb_last_error(const rlb_ctx *ctx)
 {
     return ctx ? ctx->err.c_str() : g_err.c_str();
+}
+
+const char *rlb_step_kernel(const rlb_ctx *ctx)
+{
+    if (!ctx) return "none";
+    if (ctx->fp32) {
+        if (ctx->opt.recovery_fp64) return "fp32_rec64";
+        return rlb::f32_step_kernel_name(ctx->sp, ctx->dim, ctx->opt.euler_mode);
+    }
+    return rlb::f64_step_kernel_name(ctx->sp, ctx->dim);
 }
 
 const char *rlb_status_string(int status)

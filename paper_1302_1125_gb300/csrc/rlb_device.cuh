@@ -39,7 +39,9 @@ __host__ __device__ constexpr int cdir()
 }
 
 enum { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_INLET = 2 };
-enum { ST_NONPHYSICAL = 1, ST_ASYMMETRIC = 2 };   // ST_ASYMMETRIC: a state the 2-D symmetry reduction cannot take
+enum { ST_NONPHYSICAL = 1, ST_ASYMMETRIC = 2, ST_TIMEOUT = 4 };   // ST_ASYMMETRIC: a state the 2-D symmetry
+                                                                 // reduction cannot take; ST_TIMEOUT: a bounded
+                                                                 // wait of a kernel gave up
 
 // ---------------------------------------------------------------------------
 // Macroscopic state and recovery (Sec. II: T^{0 mu} plus eps = 3P, Eq. 38)

@@ -2,6 +2,7 @@
 // the kernel translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>   // CUtensorMap (the type only; the encoder is fetched from the driver at run time)
 #include <cuda_runtime.h>
 
 namespace rlb {
@@ -20,12 +21,20 @@ struct StepParams {
     double ghost_f[19], ghost_h[19];   // inlet equilibria
     unsigned *status;        // device status word (bit 0: non-physical cell)
     int lat;                 // lattice: 0 extended (Sec. II.A), 1 basic (Sec. II)
-    int mapping;             // grids: 0 automatic, 1 tiles, 2 linear (rlb_options.thread_mapping)
+    int mapping;             // grids: 0 automatic, 1 tiles, 2 linear, 3 tiles staged by block-wide bulk
+                             // copies where eligible (rlb_options.thread_mapping)
     int sym;                 // grids: exact symmetry reduction, 1 on 1-D grids (7 planes per
                              // distribution), 2 on 2-D grids (14 planes: mirror images in z), 0 none
     // float copies for the FP32-storage kernel (no FP64 conversion on device)
     float f_k1, f_k2, f_half_lim, f_kw, f_kbulk, f_eta_over_s, f_tau_override;
     float f_ghost_f[19], f_ghost_h[19];
+};
+
+// Tensor maps of one buffer of f and h planes (x, y, z, population), with
+// boxes of a tile's centre rows (72 x 12) and of one z-neighbour plane
+// (64 x 8), for the bulk-staged FP32 step
+struct TileMaps {
+    CUtensorMap fc, fz, hc, hz;
 };
 
 // launchers (kernel translation units); dim = 1, 2 or 3, euler = 0/1; the
@@ -34,7 +43,17 @@ struct StepParams {
 cudaError_t launch_step_f64(const StepParams &p, int dim, int euler, const double *f, const double *h,
                             double *fo, double *ho, double *prev, cudaStream_t s);
 cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f, const float *h,
-                            float *fo, float *ho, float *prev, cudaStream_t s);
+                            float *fo, float *ho, float *prev, cudaStream_t s, const TileMaps *maps = nullptr);
+// the FP32-storage step on eligible 3-D grids with its stencil tiles staged by
+// bulk copies (rlb_step_f32_bulk.cu)
+bool f32_bulk_eligible(const StepParams &p, int dim, int euler);
+// encode the maps of the planes at f and h (cudaSuccess, or the failure)
+cudaError_t make_tile_maps(const StepParams &p, const float *f, const float *h, TileMaps *out);
+cudaError_t launch_step_f32_bulk(const StepParams &p, const float *f, const float *h, float *fo, float *ho,
+                                 float *prev, const TileMaps *maps, cudaStream_t s);
+// name of the step kernel launch_step_f64 / launch_step_f32 picks for p (see rlb_step_kernel)
+const char *f64_step_kernel_name(const StepParams &p, int dim);
+const char *f32_step_kernel_name(const StepParams &p, int dim, int euler);
 // the FP32-storage step with the FP64 recovery (rlb_options.recovery_fp64)
 cudaError_t launch_step_f32_rec64(const StepParams &p, int dim, const float *f, const float *h, float *fo,
                                   float *ho, float *prev, cudaStream_t s);

@@ -25,6 +25,7 @@
 
 #include <utility>
 
+#include "rlb_bulk.cuh"
 #include "rlb_classes.cuh"
 #include "rlb_device.cuh"
 #include "rlb_internal.h"
@@ -144,13 +145,19 @@ struct GlobalSrc {
     const float *q;
     const Geo &g;
     __device__ __forceinline__ f2 get(int, int off) const { return ldpair<VEC2, LD>(q, g, off); }
+    template <int A, int D>
+    __device__ __forceinline__ f2 nb(int slot, int off) const { return get(slot, off); }
 };
 
 struct StageSrc {
     const f2 *s;     // slot 0 of this thread's buffer
     int stride;      // f2 elements between slots
     __device__ __forceinline__ f2 get(int slot, int) const { return s[slot * stride]; }
+    template <int A, int D>
+    __device__ __forceinline__ f2 nb(int slot, int off) const { return get(slot, off); }
 };
+// TileSrc (rlb_bulk.cuh): the block's bulk-copied tiles; it takes the
+// neighbours along y and z by axis and distance, the x pairs by slot
 
 // x0-2 .. x0+3 of one plane.  With even nx every thread loads three aligned
 // pairs; periodic edges wrap to aligned pairs, and the clamped (open) or ghost
@@ -163,7 +170,7 @@ __device__ __forceinline__ void xstencil(const Src &src, const float *q, const G
         const f2 a = src.get(0, g.oa), b = src.get(1, 0), c = src.get(2, g.oc);
         v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y; v[4] = c.x; v[5] = c.y;
         if (g.xfix) {
-            if (g.xfix & XF_LO_CLAMP) v[1] = v[0];
+            if (g.xfix & XF_LO_CLAMP) { v[0] = v[2]; v[1] = v[2]; }
             if (g.xfix & XF_LO_GHOST) { v[0] = ghost; v[1] = ghost; }
             if (g.xfix & XF_HI_CLAMP) { v[4] = v[3]; v[5] = v[3]; }
             if (g.xfix & XF_HI_GHOST) { v[4] = ghost; v[5] = ghost; }
@@ -427,21 +434,24 @@ __device__ __forceinline__ void axis2(const Src &src, const Geo &g, const StepPa
         }
     } else {
         if constexpr (c > 0) {
-            const f2 Aq = src.get(sb, off_of<A>(g, p, -2)), B = src.get(sb + 1, off_of<A>(g, p, -1));
-            const f2 Dq = src.get(sb + 2, off_of<A>(g, p, 1));
+            const f2 Aq = src.template nb<A, -2>(sb, off_of<A>(g, p, -2));
+            const f2 B = src.template nb<A, -1>(sb + 1, off_of<A>(g, p, -1));
+            const f2 Dq = src.template nb<A, 1>(sb + 2, off_of<A>(g, p, 1));
             const f2 d0 = B - Aq, d1 = C - B, d2 = Dq - C;
             const f2 Dv = fma2(bc(hl), mm(d2, d1) - mm(d1, d0), d1);
             inc = fma2(bc(-k), Dv, inc);
             if constexpr (need_lap) lap = lap + (d2 - d1);
         } else if constexpr (c < 0) {
-            const f2 B = src.get(sb, off_of<A>(g, p, -1)), Dq = src.get(sb + 1, off_of<A>(g, p, 1));
-            const f2 Eq = src.get(sb + 2, off_of<A>(g, p, 2));
+            const f2 B = src.template nb<A, -1>(sb, off_of<A>(g, p, -1));
+            const f2 Dq = src.template nb<A, 1>(sb + 1, off_of<A>(g, p, 1));
+            const f2 Eq = src.template nb<A, 2>(sb + 2, off_of<A>(g, p, 2));
             const f2 e0 = C - B, e1 = Dq - C, e2 = Eq - Dq;
             const f2 Dv = fma2(bc(-hl), mm(e1, e2) - mm(e0, e1), e1);
             inc = fma2(bc(k), Dv, inc);
             if constexpr (need_lap) lap = lap + (e1 - e0);
         } else if constexpr (need_lap) {
-            const f2 B = src.get(sb, off_of<A>(g, p, -1)), Dq = src.get(sb + 1, off_of<A>(g, p, 1));
+            const f2 B = src.template nb<A, -1>(sb, off_of<A>(g, p, -1));
+            const f2 Dq = src.template nb<A, 1>(sb + 1, off_of<A>(g, p, 1));
             lap = lap + ((Dq - C) - (C - B));
         }
     }
@@ -554,19 +564,21 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
 // previous level's planes of the zero sums (sum c_z f; 1-D also sum c_y f)
 // are left alone.
 template <int DIM, bool EULER, bool VEC2, int LD = LD_NC, bool PARK = false, bool STAGE = false, int NP = 19,
-          int LAT = 0, bool REC64 = false>
+          int LAT = 0, bool REC64 = false, bool BULK = false>
 __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, float eos, float kb,
                                             const float *__restrict__ f, const float *__restrict__ h,
                                             float *__restrict__ fo, float *__restrict__ ho,
                                             float *__restrict__ prev, long long ps,
                                             f2 *park = nullptr, int pstride = 0,
-                                            f2 *stage = nullptr, int sstride = 0)
+                                            f2 *stage = nullptr, int sstride = 0, Bulk *bk = nullptr)
 {
     const float k1 = p.f_k1, k2 = p.f_k2, hl = p.f_half_lim;
     static_assert(!STAGE || (VEC2 && !EULER), "staging needs aligned pairs and the viscous step");
     static_assert(NP == 19 || (NP == 7 && DIM == 1 && !EULER) || (NP == 14 && DIM == 2 && !EULER),
                   "the symmetry reductions are 1-D or 2-D and viscous");
     static_assert(!REC64 || (!EULER && NP == 19), "the FP64 recovery is a variant of the viscous 19-population step");
+    static_assert(!BULK || (DIM == 3 && VEC2 && !EULER && NP == 19 && !STAGE),
+                  "bulk-copied tiles: the viscous 3-D step with aligned pairs");
     constexpr int NI = 2 * NP;   // items: f classes, then h classes
     unsigned sdst0 = 0;
     if constexpr (STAGE) {
@@ -582,7 +594,36 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
         constexpr int I = rep<NP>(IS_F ? J : J - NP);
         const float *q = (IS_F ? f : h) + I * ps;
         const float ghost = IS_F ? p.f_ghost_f[I] : p.f_ghost_h[I];
-        if constexpr (STAGE) {
+        if constexpr (BULK) {
+            constexpr int b = J % kBulkBufs;
+            constexpr unsigned par = unsigned(J / kBulkBufs) & 1u;
+            if (!bk->failed && !mbar_wait(&bk->full[b], par)) {
+                bk->failed = true;
+                atomicOr(p.status, unsigned(ST_TIMEOUT));
+            }
+            bk->failed = __any_sync(0xffffffffu, bk->failed);   // warp-uniform: the issue below is warp-wide
+            const TileSrc src{bk->ctr + b * kTileFloats, bk->zpl + b * kTileFloats};
+            const f2 r = streamed2<DIM, IS_F, I, VEC2, LD, LAT>(src, q, g, p, ghost, k1, k2, hl, kb);
+            // this warp is done with buffer b: it counts itself out, and the
+            // warp that counts the last of the 8 refills the buffer with item
+            // J + kBulkBufs (release fence before the count, acquire after
+            // it, then the generic-to-async proxy fence before the copies
+            // overwrite what the other warps read)
+            if constexpr (J + kBulkBufs < NI) {
+                __syncwarp();
+                int last = 0;
+                if (bk->lane == 0) {
+                    asm volatile("fence.acq_rel.cta;" ::: "memory");
+                    last = (atomicAdd(&bk->done[b], 1) & 7) == 7;
+                    if (last) asm volatile("fence.acq_rel.cta;" ::: "memory");
+                }
+                if (__shfl_sync(0xffffffffu, last, 0) && !bk->failed) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bulk_issue<NP, J + kBulkBufs, LAT>(*bk, p, f, h, ps);
+                }
+            }
+            return r;
+        } else if constexpr (STAGE) {
             if constexpr (J + kStageAhead < NI) {
                 stage_item<DIM, NP, J + kStageAhead, LAT>(f, h, g, p, ps, sdst0, unsigned(sstride * sizeof(f2)));
                 cp_wait<kStageAhead>();
@@ -851,7 +892,10 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
             g.zoff[k] = DIM > 2 ? (map1(z + ds[k], p.nz, p.bc_lo[2], p.bc_hi[2], gh) - z) * p.nx * p.ny : 0;
         }
     }
-    const int nthr = blockDim.x * blockDim.y;
+    // threads per block as the launcher sets them (rlb_step_f32_launch.cuh), a
+    // compile-time constant so that the shared-memory slots of this thread
+    // sit at fixed offsets from one base address
+    constexpr int nthr = (DIM == 1 && !LIN) ? 128 : 32 * RLB_F32_BY;
     const int tid = threadIdx.x + blockDim.x * threadIdx.y;
     constexpr bool STAGE = kStageOn && VEC2 && !EULER;
     update_pair<DIM, EULER, VEC2, LD_NC, kParkOn, STAGE, NP, LAT, REC64>(p, g, p.f_eta_over_s, p.f_kbulk, f, h, fo, ho,

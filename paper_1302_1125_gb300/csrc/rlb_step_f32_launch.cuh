@@ -14,7 +14,7 @@ namespace rlb {
 // 64 x BY-cell tiles would leave more than 3 % of their lanes idle
 inline bool f32_use_linear(const StepParams &p, int dim)
 {
-    if (dim == 1 || p.mapping == 1) return false;
+    if (dim == 1 || p.mapping == 1 || p.mapping == 3) return false;   // 3: tiles (bulk-staged where eligible)
     if (p.mapping == 2) return true;
     const long long npairs = (p.nx + 1) / 2;
     const long long tiles_x = (npairs + 31) / 32, tiles_y = (p.ny + RLB_F32_BY - 1) / RLB_F32_BY;

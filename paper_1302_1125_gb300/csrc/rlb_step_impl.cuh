@@ -31,7 +31,7 @@ cudaError_t launch_step_np(const StepParams &p, const T *f, const T *h, T *fo, T
     // 32 x 16 x 16 grids.  The step time of such grids stays set by one
     // warp's FP64 instructions at one scheduler's FP64 rate.
     const int nsm = sm_count();
-    if (cells < 128LL * nsm && p.mapping != 1) {
+    if (cells < 128LL * nsm && p.mapping != 1 && p.mapping != 3) {   // 3: tiles (FP32: bulk-staged)
         int bs = int(((cells + nsm - 1) / nsm + 31) / 32 * 32);
         bs = bs < 32 ? 32 : (bs > 128 ? 128 : bs);
         const unsigned nb = unsigned((cells + bs - 1) / bs);

@@ -70,6 +70,8 @@ def arg_parser():
                     help="fp32_rec64: FP32 storage with the FP64 recovery (recovery_fp64 = 1)")
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
+    ap.add_argument("--mapping", type=int, default=0,
+                    help="grids: rlb_options.thread_mapping (3: tiles with per-thread staging)")
     ap.add_argument("--tuning", default="", help="batch launch shape threads,bound,cluster,pairs_per_thread")
     ap.add_argument("--symmetry", action="store_true", help="batch: the 1-D symmetry reduction")
     return ap
@@ -82,7 +84,8 @@ def main():
         return run_batch(a)
     w = MAKERS[a.workload](a.scale)
     prec = rlb.FP64 if a.precision == "fp64" else rlb.FP32_STORAGE
-    g = rlb.Grid.from_workload(w, precision=prec, recovery_fp64=int(a.precision == "fp32_rec64"))
+    g = rlb.Grid.from_workload(w, precision=prec, recovery_fp64=int(a.precision == "fp32_rec64"),
+                               thread_mapping=a.mapping)
     g.init(*[torch.as_tensor(x, device="cuda") for x in w.fields()])
     g.step(a.warmup)
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -92,7 +95,7 @@ def main():
     e.record()
     torch.cuda.synchronize()
     ms = s.elapsed_time(e) / max(a.steps, 1)
-    print(json.dumps({"workload": w.name, "cells": w.N, "precision": a.precision,
+    print(json.dumps({"workload": w.name, "cells": w.N, "precision": a.precision, "kernel": g.step_kernel,
                       "ms_per_step": ms, "mlups": w.N / (ms * 1e-3) / 1e6}))
 
 

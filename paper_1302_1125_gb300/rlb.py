@@ -23,7 +23,8 @@ LIMITER_MINMOD, LIMITER_NONE = 0, 1
 BC_PERIODIC, BC_OUTFLOW, BC_INLET = 0, 1, 2
 FP64, FP32_STORAGE = 0, 1
 MODEL_EXTENDED, MODEL_BASIC = 0, 1
-MAPPING_AUTO, MAPPING_TILES, MAPPING_LINEAR = 0, 1, 2   # rlb_options.thread_mapping
+# rlb_options.thread_mapping; MAPPING_BULK_TILES: tiles staged by block-wide bulk copies
+MAPPING_AUTO, MAPPING_TILES, MAPPING_LINEAR, MAPPING_BULK_TILES = 0, 1, 2, 3
 Q = 19
 
 
@@ -100,6 +101,8 @@ def lib() -> C.CDLL:
         L.rlb_last_error.restype = C.c_char_p
         L.rlb_status_string.argtypes = [C.c_int]
         L.rlb_status_string.restype = C.c_char_p
+        L.rlb_step_kernel.argtypes = [C.c_void_p]
+        L.rlb_step_kernel.restype = C.c_char_p
         L.rlb_set_solid.argtypes = [ctxp, vp, C.c_double, C.c_double, C.c_int]
         L.rlb_set_solid.restype = C.c_int
         L.rlb_conserved_totals_noalloc.argtypes = [vp, vp, C.c_int, C.c_longlong, C.c_int, vp, vp]
@@ -139,6 +142,10 @@ def lib() -> C.CDLL:
 
 def status_string(status: int) -> str:
     return lib().rlb_status_string(int(status)).decode()
+
+
+def rlb_step_kernel(ctx) -> str:
+    return lib().rlb_step_kernel(ctx).decode()
 
 
 def last_error(ctx=None) -> str:
@@ -329,6 +336,11 @@ class Grid:
     def step(self, nsteps=1):
         rlb_step(self.ctx, nsteps)
         return self
+
+    @property
+    def step_kernel(self) -> str:
+        """name of the step kernel this grid's steps launch (rlb_step_kernel)"""
+        return rlb_step_kernel(self.ctx)
 
     def set_solid(self, mask, n, T):
         """hold the cells where mask != 0 at the equilibrium of (n, T, u = 0)

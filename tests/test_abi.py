@@ -88,7 +88,8 @@ def cfg(**kw):
     ({"symmetry_1d": 1, "precision": 1, "bc_lo": (2, 0, 0),
       "inlet": (1.0, 1.0, (0.5, 0.1, 0.0))}, rlb.RLB_E_INVALID),          # inlet moving in y
     ({"model": 2}, rlb.RLB_E_INVALID),
-    ({"thread_mapping": 3}, rlb.RLB_E_INVALID),
+    ({"thread_mapping": 4}, rlb.RLB_E_INVALID),
+    ({"thread_mapping": 3, "ny": 8, "nz": 8}, rlb.RLB_OK),
     ({"thread_mapping": -1}, rlb.RLB_E_INVALID),
     ({"thread_mapping": 2, "ny": 8, "nz": 8}, rlb.RLB_OK),
     ({"symmetry_2d": 1, "ny": 8, "precision": 1}, rlb.RLB_OK),

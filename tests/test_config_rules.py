@@ -46,7 +46,7 @@ def expected(nx, ny, nz, lo, hi, inlet_n, inlet_T, inlet_u, eta, zeta, limiter, 
     invalid |= limiter not in (0, 1)
     invalid |= not (o["dt"] > 0 and math.isfinite(o["dt"]))
     invalid |= o["precision"] not in (0, 1) or o["euler"] not in (0, 1) or o["model"] not in (0, 1)
-    invalid |= o["sym1"] not in (0, 1) or o["sym2"] not in (0, 1) or o["mapping"] not in (0, 1, 2)
+    invalid |= o["sym1"] not in (0, 1) or o["sym2"] not in (0, 1) or o["mapping"] not in (0, 1, 2, 3)
     if o["sym1"] == 1:
         invalid |= o["euler"] != 0 or ny != 1 or nz != 1 or (has_inlet and (inlet_u[1] != 0 or inlet_u[2] != 0))
     if o["sym2"] == 1:
@@ -83,7 +83,7 @@ vel = st.sampled_from([0.0, 0.3, -0.6, 0.9, 1.0])
            dt=st.sampled_from([0.0, 0.05, 0.15, 0.25, 0.3, 0.4, 0.6, math.nan]),
            precision=st.sampled_from([0, 1, 2]), euler=st.sampled_from([0, 1, 2]),
            sym1=st.sampled_from([0, 1, 2]), sym2=st.sampled_from([0, 1, 2]),
-           model=st.sampled_from([0, 1, 2]), mapping=st.sampled_from([-1, 0, 1, 2, 3]),
+           model=st.sampled_from([0, 1, 2]), mapping=st.sampled_from([-1, 0, 1, 2, 3, 4]),
            tau=st.sampled_from([0.0, 0.8, math.inf]),
            alpha=st.sampled_from([-1.0, 0.0, 0.05, 0.2, 0.5, math.nan]),
            rec64=st.sampled_from([0, 0, 1, 1, 2]))

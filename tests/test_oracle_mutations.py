@@ -16,7 +16,9 @@ mistyped weight, doubled diagonals, swapped number weights; Euler mode
 Eq. 57 applied to the number distribution as well; an inlet ghost whose
 pressure drops the temperature; open ends that reflect instead of copying
 the edge cell; the h equation relaxing to h^eq(t) instead of the
-extrapolated 2 h^eq(t) - h^eq(t - dt).
+extrapolated 2 h^eq(t) - h^eq(t - dt), and the f equation doing the same;
+nu = 1 in place of sqrt(13) in every constant of the extended lattice (the
+survey's reading, which the tests of the readings reject).
 """
 import os
 import subprocess
@@ -69,6 +71,11 @@ MUTATIONS = {
                                  "orc_feq(p->inlet_n, up, k->ghost_f);"),
     "outflow_ghosts_reflecting": ("if (bc == ORC_BC_OUTFLOW) return c < 0 ? 0 : n - 1;",
                                   "if (bc == ORC_BC_OUTFLOW) return c < 0 ? -c : 2 * n - 2 - c;"),
+    "equilibrium_not_extrapolated": (
+        "fo[i] = (f[i] + sf[i] + omega * (2.0 * feq[i] - feqp[i])) / (1.0 + omega);",
+        "fo[i] = (f[i] + sf[i] + omega * feq[i]) / (1.0 + omega);"),
+    "nu_one_everywhere": ("const double nu = basic ? sqrt(19.0) : sqrt(13.0);",
+                          "const double nu = basic ? sqrt(19.0) : 1.0;"),
     "number_equilibrium_not_extrapolated": (
         "ho[i] = (h[i] + sh[i] + omega * (2.0 * heq[i] - heqp[i])) / (1.0 + omega);",
         "ho[i] = (h[i] + sh[i] + omega * heq[i]) / (1.0 + omega);"),
