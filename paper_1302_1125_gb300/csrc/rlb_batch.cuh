@@ -121,10 +121,12 @@ __global__ void __launch_bounds__(MAXT, 1) tubes_kernel(const Args a)
                     const bool odd = ((s_par[i] + s) & 1) != 0;
                     const float *f = odd ? a.f1 : a.f0, *h = odd ? a.h1 : a.h0;
                     float *fo = odd ? a.f0 : a.f1, *ho = odd ? a.h0 : a.h1;
+                    // the slots of the shared-memory arrays are MAXT apart (the
+                    // launch bound, a compile-time constant: fixed offsets
+                    // from one base address), whatever blockDim.x <= MAXT is
                     f32::update_pair<1, false, true, LD, f32::kParkOn, f32::kStageOn, NP>(
-                        a.p, g, s_eos[i], s_kb[i], f, h, fo, ho, a.prev, a.ps, s_dyn + threadIdx.x,
-                        int(blockDim.x), s_dyn + (f32::kParkOn ? f32::kParkSlots * blockDim.x : 0) + threadIdx.x,
-                        int(blockDim.x));
+                        a.p, g, s_eos[i], s_kb[i], f, h, fo, ho, a.prev, a.ps, s_dyn + threadIdx.x, MAXT,
+                        s_dyn + (f32::kParkOn ? f32::kParkSlots * MAXT : 0) + threadIdx.x, MAXT);
                 }
             }
             if (C > 1) cluster_barrier();
@@ -142,7 +144,7 @@ cudaError_t launch_variant(const Args &a, int threads, int cluster, cudaStream_t
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nclusters_out ? unsigned(cluster) : unsigned(a.nclusters * cluster), 1, 1);
     cfg.blockDim = dim3(unsigned(threads), 1, 1);
-    const size_t smem = f32::step_smem_bytes(threads, f32::kStageOn, 1);
+    const size_t smem = f32::step_smem_bytes(MAXT, f32::kStageOn, 1);   // slots MAXT apart
     cfg.dynamicSmemBytes = smem;
     if (smem > 48 * 1024) {
         const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
