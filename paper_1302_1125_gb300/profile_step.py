@@ -71,7 +71,7 @@ def arg_parser():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--mapping", type=int, default=0,
-                    help="grids: rlb_options.thread_mapping (3: tiles with per-thread staging)")
+                    help="grids: rlb_options.thread_mapping (0 automatic, 1 tiles, 2 linear, 3 tiles staged by block-wide bulk copies)")
     ap.add_argument("--tuning", default="", help="batch launch shape threads,bound,cluster,pairs_per_thread")
     ap.add_argument("--symmetry", action="store_true", help="batch: the 1-D symmetry reduction")
     return ap

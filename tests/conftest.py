@@ -8,6 +8,15 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+# The property tests of the configuration rules need hypothesis, which not
+# every machine that runs this suite has; there they are left out of the
+# collection (they are CPU tests: the GPU selection has nothing to skip).
+try:
+    import hypothesis  # noqa: F401
+except ImportError:
+    collect_ignore = ["test_config_rules.py"]
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built librlb.so")
 
