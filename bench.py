@@ -805,8 +805,8 @@ def run_ours(args):
                               "hbm_frac": BYTES_FP32 * N / (mss / args.steps * 1e-3) / 1e9 / hbm_peak,
                               "step_kernel": kernel_s,
                               "what": "the same FP32-storage step with each population's stencil tile staged "
-                                      "into shared memory by block-wide bulk copies (cp.async.bulk row "
-                                      "segments on mbarriers; thread_mapping 3)"},
+                                      "into shared memory by block-wide bulk copies (tensor-map boxes, "
+                                      "cp.async.bulk.tensor, on mbarriers; thread_mapping 3)"},
         "fp32_rec64": {"value": value_r, "unit": UNIT, "ms_per_step": msr / args.steps,
                        "hbm_frac": BYTES_FP32 * N / (msr / args.steps * 1e-3) / 1e9 / hbm_peak,
                        "precision": "FP32 populations, double-float moment sums, Landau-frame recovery of both "

@@ -121,10 +121,10 @@ typedef struct {
                               * lanes whatever nx and ny; 3: tiles, and in the FP32-storage form
                               * on grids that allow it (3-D, viscous, extended lattice, nx a
                               * multiple of 64, ny of 8, x faces not periodic) the block stages
-                              * each population's stencil tile into shared memory by bulk copies
-                              * instead of each thread staging its own (see rlb_step_kernel;
-                              * measured slower on the 512 x 256 x 256 cloud, so not the
-                              * default).  The results are the same bit for bit. */
+                              * each population's stencil tile into shared memory by tensor-map
+                              * bulk copies instead of each thread staging its own, when the
+                              * driver provides the tensor-map encoder (see rlb_step_kernel).
+                              * The results are the same bit for bit. */
     int symmetry_2d;         /* 1 (grids with nz = 1 < ny, either precision, viscous step): exact 2-D
                               * symmetry reduction.  With u_z = 0 in every cell (and at the
                               * inlet) the state is its own mirror image in z, so mirror-image
@@ -274,7 +274,8 @@ RLB_API const char *rlb_status_string(int status);
  * diagnostic; the paper has no counterpart): "fp32_bulk_tiles" (FP32
  * storage on 3-D grids whose stencil tiles are staged by block-wide bulk
  * copies: thread_mapping 3, viscous step, extended lattice, nx a multiple
- * of 64, ny of 8, x faces not periodic), "fp32_tiles" (tiles of
+ * of 64, ny of 8, x faces not periodic, tensor maps made at rlb_create),
+ * "fp32_tiles" (tiles of
  * 64 x 8 cells, each thread loading its own stencil, staged by asynchronous
  * copies in the viscous step), "fp32_linear", "fp32_1d", "fp32_rec64" (recovery_fp64),
  * "fp64_tiles", "fp64_linear", "fp64_small" (blocks of one to four warps

@@ -372,7 +372,7 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
         sp.f_ghost_h[i] = float(sp.ghost_h[i]);
     }
     // the bulk-staged FP32 tiles copy the centre rows and z-neighbour planes
-    // as tensor-map boxes; without the maps they copy row by row
+    // as tensor-map boxes; without the maps the per-thread staged kernel runs
     if (ctx->fp32 && !o.recovery_fp64 && rlb::f32_bulk_eligible(sp, ctx->dim, o.euler_mode)) {
         ctx->have_tmaps = rlb::make_tile_maps(sp, (const float *)ctx->fbuf[0], (const float *)ctx->hbuf[0],
                                               &ctx->tmaps[0]) == cudaSuccess &&
@@ -607,7 +607,7 @@ const char *rlb_step_kernel(const rlb_ctx *ctx)
     if (!ctx) return "none";
     if (ctx->fp32) {
         if (ctx->opt.recovery_fp64) return "fp32_rec64";
-        return rlb::f32_step_kernel_name(ctx->sp, ctx->dim, ctx->opt.euler_mode);
+        return rlb::f32_step_kernel_name(ctx->sp, ctx->dim, ctx->opt.euler_mode, ctx->have_tmaps);
     }
     return rlb::f64_step_kernel_name(ctx->sp, ctx->dim);
 }

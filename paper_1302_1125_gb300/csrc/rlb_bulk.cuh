@@ -1,32 +1,35 @@
 // rlb_bulk.cuh -- block-level staging of the stencil tiles of the FP32 step by
-// bulk copies (the GB300 copy engine, cp.async.bulk), for 3-D grids.
+// the copy engine (tensor-map bulk copies, cp.async.bulk.tensor), for 3-D
+// grids.
 //
 // A block of 32 x 8 threads updates a tile of 64 x 8 cells in one z-plane
 // (two x-adjacent cells per thread).  For each of its 38 items (f classes,
 // then h classes) the block needs, from the population's plane:
 //   the tile's own rows with the y neighbours the item streams or diffuses
 //   over (rows y0 - 2 .. y0 + 9 at most), 72 values wide (x0 - 4 .. x0 + 67,
-//   the x neighbours) or 64 when the item does not move along x and has no
-//   Laplacian there;
+//   the x neighbours);
 //   the tile's 8 rows in the z-neighbour planes it needs (z - 2, z - 1,
 //   z + 1, z + 2 at most), 64 values wide.
-// Each such row segment is one bulk copy (288 or 256 bytes, 16-byte aligned)
-// from global memory into one of kBulkBufs shared-memory buffers, completed
-// on that buffer's "full" mbarrier (expect-tx with the item's byte count).
-// The copies of item J + kBulkBufs go into item J's buffer once every warp
-// is done with item J: each warp counts itself out on the buffer's counter
-// (an atomic add after a release fence), and the warp that counts the last
-// one issues them, its lanes one copy each, so no warp waits for another to
-// finish.  Threads then read their stencil from the tile at fixed offsets:
-// no per-thread address arithmetic and no per-thread copies.
-// With tensor maps (the default) the centre rows are one 72 x 12 box and each
-// z-neighbour plane one 64 x 8 box; tiles whose y halo crosses a y face, or
-// grids without maps, copy the centre rows row by row.
+// The centre rows arrive as one 72 x 12 tensor box, each z-neighbour plane as
+// one 64 x 8 box, into one of kBulkBufs shared-memory buffers, completed on
+// that buffer's "full" mbarrier (expect-tx with the item's byte count).  A
+// tile whose y halo crosses a y face takes its centre rows as row copies
+// (cp.async.bulk) from the rows the y boundary map picks (a 72 x 12 box
+// would read zeros there; 72 x 1 boxes cannot land on rows that are not
+// 128-byte aligned, as tensor copies into shared memory must).  The copies
+// of item J + kBulkBufs go into item J's buffer once every warp is done with
+// item J: each warp counts itself out on the buffer's counter (an atomic add
+// after a release fence), and the warp that counts the last one issues
+// them, a few lanes one copy each, so no warp waits for another to finish.
+// Threads then read their stencil from the tile at fixed offsets: no
+// per-thread address arithmetic and no per-thread copies.  The boundary maps
+// of the block's rows and planes are computed once, into shared memory, so
+// the issue of an item is a few instructions (the 38 items are unrolled:
+// their code has to stay small enough for the instruction cache).
 //
-// Source rows are chosen through the y and z boundary maps (periodic wrap or
-// zero-gradient clamp), so the tile holds the mapped neighbours.  The x
-// faces must not be periodic: at the grid's x ends the halo columns are not
-// copied, and the edge threads' clamp or ghost fix-ups replace them.
+// At the grid's x ends the halo columns are not data (boxes read zeros
+// there, row copies leave them alone), and the edge threads' clamp or ghost
+// fix-ups replace them, so the x faces must not be periodic.
 //
 // Every wait is bounded (about a second of clock cycles): on a timeout the
 // thread sets ST_TIMEOUT in the status word, stops waiting and issuing, and
@@ -90,20 +93,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // aligned), completing as transaction bytes on bar
 __device__ __forceinline__ void bulk_g2s(float *dst, const float *src, unsigned bytes, unsigned long long *bar)
 {
-#ifdef RLB_BULK_DST_CLUSTER
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst)),
-                 "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
-                 : "memory");
-#else
     asm volatile("cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                      smem_addr(dst)),
                  "l"(__cvta_generic_to_global(src)), "r"(bytes), "r"(smem_addr(bar))
                  : "memory");
-#endif
 }
 // the box of tensor map `map` at element coordinates (x, y, z, plane) into
-// shared dst (16-byte aligned), completing on bar with the box's full size
+// shared dst (128-byte aligned), completing on bar with the box's full size
 // (elements outside the tensor arrive as zeros)
 __device__ __forceinline__ void tma_g2s(float *dst, const CUtensorMap *map, int x, int y, int z, int plane,
                                         unsigned long long *bar)
@@ -123,11 +119,13 @@ struct Bulk {
     unsigned long long *full;     // [kBulkBufs] (shared)
     int *done;                    // [kBulkBufs] (shared): warps that finished with each buffer, cumulative
     int *issued;                  // [kBulkBufs] (shared): phases issued per buffer
+    const int *ymap;              // [12] (shared): grid row of centre row t (y0 - 2 + t through the y map)
+    const int *zmap;              // [4] (shared): grid plane of z - 2, z - 1, z + 1, z + 2 through the z map
     int warp, lane;
     int x0t, y0, z;               // tile origin
-    int cxlo, cxhi;               // x range copied into centre rows that need the x neighbours
-    const TileMaps *maps;         // tensor maps of f and h (null: row-by-row copies)
-    bool rows;                    // centre rows copied row by row (no maps, or a y-edge tile)
+    int cxlo, cxhi;               // x range of the centre row copies (the tile's x halo, inside the grid)
+    const TileMaps *maps;         // tensor maps of f and h
+    bool rows;                    // centre rows by row copies (a y-edge tile)
     bool failed;
 };
 
@@ -177,73 +175,37 @@ struct ItemRows {
     static constexpr int klo = cz > 0 ? 0 : ((cz < 0 || lap) ? 1 : 4);
     static constexpr int khi = cz < 0 ? 4 : ((cz > 0 || lap) ? 3 : 4);
     static constexpr int nc = thi - tlo;
-    static constexpr int nrows = nc + 8 * (khi - klo);
 };
 
-// issue the copies of item J into buffer J % kBulkBufs (called by a whole warp)
+// issue the copies of item J into buffer J % kBulkBufs (called by a whole
+// warp): lanes 0 .. nz - 1 the z-neighbour planes, lane 31 the centre box,
+// or lanes 4 .. 4 + nc - 1 the centre rows of a y-edge tile
 template <int NP, int J, int LAT>
-__device__ __forceinline__ void bulk_issue(Bulk &b, const StepParams &p, const float *f, const float *h, long long ps)
+__device__ __forceinline__ void bulk_issue(Bulk &b, const StepParams &p, const float *f, const float *h)
 {
     using R = ItemRows<NP, J, LAT>;
     constexpr int buf = J % kBulkBufs;
-    if (b.maps) {
-        // tensor boxes: the 72 x 12 centre tile (unless the tile's y halo
-        // needs the boundary map: row copies below) and one 64 x 8 box per
-        // z-neighbour plane
-        constexpr int nz = R::khi - R::klo;
-        const unsigned cbytes = b.rows ? unsigned(R::nc) * unsigned((R::xneed ? b.cxhi - b.cxlo : 64) * 4)
-                                       : unsigned(kCentreFloats * 4);
-        if (b.lane == 0) {
-            mbar_expect_tx(&b.full[buf], cbytes + unsigned(nz) * unsigned(kPlaneFloats * 4));
-            b.issued[buf] += 1;
-        }
-        __syncwarp();
-        const CUtensorMap *mc = R::IS_F ? &b.maps->fc : &b.maps->hc;
-        const CUtensorMap *mz = R::IS_F ? &b.maps->fz : &b.maps->hz;
-        float *dst0 = b.tile + buf * kTileFloats;
-        if (b.lane < nz) {
-            const int k = R::klo + b.lane;
-            const int d = k < 2 ? k - 2 : k - 1;
-            const int zm = bulk_map(b.z + d, p.nz, p.bc_lo[2], p.bc_hi[2]);
-            tma_g2s(dst0 + kCentreFloats + k * kPlaneFloats, mz, b.x0t, b.y0, zm, R::I, &b.full[buf]);
-        }
-        if (!b.rows) {
-            if (b.lane == 31) tma_g2s(dst0, mc, b.x0t - 4, b.y0 - 2, b.z, R::I, &b.full[buf]);
-        } else if (b.lane < R::nc) {
-            const int xlo = R::xneed ? b.cxlo : b.x0t;
-            const int t = R::tlo + b.lane;
-            const int y = bulk_map(b.y0 - 2 + t, p.ny, p.bc_lo[1], p.bc_hi[1]);
-            const float *q = (R::IS_F ? f : h) + R::I * ps;
-            bulk_g2s(dst0 + t * kRowC + (xlo - (b.x0t - 4)), q + b.z * (long long)p.nx * p.ny + (long long)y * p.nx + xlo,
-                     cbytes / unsigned(R::nc), &b.full[buf]);
-        }
-        return;
-    }
-    const int xlo = R::xneed ? b.cxlo : b.x0t;
-    const int xhi = R::xneed ? b.cxhi : b.x0t + 64;
-    const unsigned cbytes = unsigned(xhi - xlo) * 4u;
+    constexpr int nz = R::khi - R::klo;
+    constexpr unsigned zbytes = unsigned(nz * kPlaneFloats * 4);
+    const unsigned rowbytes = unsigned(b.cxhi - b.cxlo) * 4u;
     if (b.lane == 0) {
-        mbar_expect_tx(&b.full[buf], unsigned(R::nc) * cbytes + unsigned(R::nrows - R::nc) * 256u);
+        mbar_expect_tx(&b.full[buf], b.rows ? unsigned(R::nc) * rowbytes + zbytes : unsigned(kCentreFloats * 4) + zbytes);
         b.issued[buf] += 1;
     }
     __syncwarp();
-    const float *q = (R::IS_F ? f : h) + R::I * ps;
     float *dst0 = b.tile + buf * kTileFloats;
-    const long long plane = (long long)p.nx * p.ny;
-    for (int r = b.lane; r < R::nrows; r += 32) {
-        if (r < R::nc) {
-            const int t = R::tlo + r;
-            const int y = bulk_map(b.y0 - 2 + t, p.ny, p.bc_lo[1], p.bc_hi[1]);
-            bulk_g2s(dst0 + t * kRowC + (xlo - (b.x0t - 4)), q + b.z * plane + (long long)y * p.nx + xlo, cbytes,
-                     &b.full[buf]);
-        } else {
-            const int rr = r - R::nc;
-            const int k = R::klo + rr / 8, t = rr % 8;
-            const int d = k < 2 ? k - 2 : k - 1;
-            const int zm = bulk_map(b.z + d, p.nz, p.bc_lo[2], p.bc_hi[2]);
-            bulk_g2s(dst0 + kCentreFloats + k * kPlaneFloats + t * 64,
-                     q + zm * plane + (long long)(b.y0 + t) * p.nx + b.x0t, 256u, &b.full[buf]);
-        }
+    if (b.lane < nz) {
+        const int k = R::klo + b.lane;
+        tma_g2s(dst0 + kCentreFloats + k * kPlaneFloats, R::IS_F ? &b.maps->fz : &b.maps->hz, b.x0t, b.y0, b.zmap[k],
+                R::I, &b.full[buf]);
+    }
+    if (!b.rows) {
+        if (b.lane == 31) tma_g2s(dst0, R::IS_F ? &b.maps->fc : &b.maps->hc, b.x0t - 4, b.y0 - 2, b.z, R::I, &b.full[buf]);
+    } else if (b.lane >= 4 && b.lane < 4 + R::nc) {
+        const int t = R::tlo + b.lane - 4;
+        const float *q = (R::IS_F ? f : h) + R::I * p.ps;
+        bulk_g2s(dst0 + t * kRowC + (b.cxlo - (b.x0t - 4)),
+                 q + (long long)(b.z * p.ny + b.ymap[t]) * p.nx + b.cxlo, rowbytes, &b.full[buf]);
     }
 }
 

@@ -45,7 +45,8 @@ cudaError_t launch_step_f64(const StepParams &p, int dim, int euler, const doubl
 cudaError_t launch_step_f32(const StepParams &p, int dim, int euler, const float *f, const float *h,
                             float *fo, float *ho, float *prev, cudaStream_t s, const TileMaps *maps = nullptr);
 // the FP32-storage step on eligible 3-D grids with its stencil tiles staged by
-// bulk copies (rlb_step_f32_bulk.cu)
+// bulk copies (rlb_step_f32_bulk.cu); it needs the tensor maps of the buffers
+// it reads (launch_step_f32 runs the per-thread staged kernel without them)
 bool f32_bulk_eligible(const StepParams &p, int dim, int euler);
 // encode the maps of the planes at f and h (cudaSuccess, or the failure)
 cudaError_t make_tile_maps(const StepParams &p, const float *f, const float *h, TileMaps *out);
@@ -53,7 +54,7 @@ cudaError_t launch_step_f32_bulk(const StepParams &p, const float *f, const floa
                                  float *prev, const TileMaps *maps, cudaStream_t s);
 // name of the step kernel launch_step_f64 / launch_step_f32 picks for p (see rlb_step_kernel)
 const char *f64_step_kernel_name(const StepParams &p, int dim);
-const char *f32_step_kernel_name(const StepParams &p, int dim, int euler);
+const char *f32_step_kernel_name(const StepParams &p, int dim, int euler, bool have_maps);
 // the FP32-storage step with the FP64 recovery (rlb_options.recovery_fp64)
 cudaError_t launch_step_f32_rec64(const StepParams &p, int dim, const float *f, const float *h, float *fo,
                                   float *ho, float *prev, cudaStream_t s);

@@ -619,7 +619,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
                 }
                 if (__shfl_sync(0xffffffffu, last, 0) && !bk->failed) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bulk_issue<NP, J + kBulkBufs, LAT>(*bk, p, f, h, ps);
+                    bulk_issue<NP, J + kBulkBufs, LAT>(*bk, p, f, h);
                 }
             }
             return r;

@@ -4,12 +4,9 @@
 // planes, extended lattice, nx a multiple of 64 and ny a multiple of 8 (every
 // block a full 64 x 8 tile, so that all its threads take part in the
 // barriers), x faces not periodic, and rlb_options.thread_mapping = 3 (an
-// option: on the 512 x 256 x 256 grid this kernel is slower than the
-// per-thread staged one); the launcher in rlb_step_f32.cu falls back to the
-// per-thread staged kernel otherwise.
+// option); the launcher in rlb_step_f32.cu runs the per-thread staged kernel
+// otherwise, and also when the tensor maps could not be made.
 #include <cudaTypedefs.h>   // PFN_cuTensorMapEncodeTiled
-
-#include <cstring>
 
 #include "rlb_step_f32_launch.cuh"
 
@@ -17,20 +14,20 @@ namespace rlb {
 namespace f32 {
 
 constexpr int kBulkThreads = 256;   // 32 x 8
-// dynamic shared memory: tiles, parked h coefficients, mbarriers, counters
+// dynamic shared memory: tiles, parked h coefficients, mbarriers, counters,
+// the row and plane maps
 constexpr size_t bulk_smem_bytes()
 {
     return sizeof(float) * size_t(kBulkBufs) * kTileFloats + sizeof(f2) * size_t(kParkSlots) * kBulkThreads +
-           sizeof(unsigned long long) * kBulkBufs + 2 * sizeof(int) * kBulkBufs;
+           sizeof(unsigned long long) * kBulkBufs + 2 * sizeof(int) * kBulkBufs + sizeof(int) * 16;
 }
 
-// maps: tensor maps of f and h (have_maps = 0: the centre rows and planes are
-// copied row by row instead)
+// maps: tensor maps of the f and h buffers the step reads
 template <int LAT>
 __global__ void __launch_bounds__(kBulkThreads, 2)
     step_f32_bulk_kernel(const StepParams p, const float *__restrict__ f, const float *__restrict__ h,
                          float *__restrict__ fo, float *__restrict__ ho, float *__restrict__ prev,
-                         const __grid_constant__ TileMaps maps, int have_maps)
+                         const __grid_constant__ TileMaps maps)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float *tiles = reinterpret_cast<float *>(smem);
@@ -39,6 +36,7 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
         smem + sizeof(float) * size_t(kBulkBufs) * kTileFloats + sizeof(f2) * size_t(kParkSlots) * kBulkThreads);
     int *issued = reinterpret_cast<int *>(bars + kBulkBufs);
     int *done = issued + kBulkBufs;
+    int *ymap = done + kBulkBufs, *zmap = ymap + 12;
 
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = tx + 32 * ty;
@@ -54,10 +52,12 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
     b.z = int(blockIdx.z);
     b.cxlo = b.x0t == 0 ? 0 : b.x0t - 4;
     b.cxhi = b.x0t + 64 == p.nx ? p.nx : b.x0t + 68;
-    b.maps = have_maps ? &maps : nullptr;
-    // tensor boxes zero-fill outside the grid: tiles whose y halo crosses a
+    b.ymap = ymap;
+    b.zmap = zmap;
+    b.maps = &maps;
+    // tensor boxes read zeros outside the grid: tiles whose y halo crosses a
     // y face copy their centre rows row by row, through the boundary map
-    b.rows = !have_maps || b.y0 < 2 || b.y0 + 10 > p.ny;
+    b.rows = b.y0 < 2 || b.y0 + 10 > p.ny;
     b.failed = false;
     b.ctr = tiles + (ty + 2) * kRowC + 2 * tx + 4;
     b.zpl = tiles + kCentreFloats + ty * 64 + 2 * tx;
@@ -69,12 +69,18 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    if (tid >= 32 && tid < 44) {
+        ymap[tid - 32] = bulk_map(b.y0 - 2 + (tid - 32), p.ny, p.bc_lo[1], p.bc_hi[1]);
+    } else if (tid >= 64 && tid < 68) {
+        const int k = tid - 64;
+        zmap[k] = bulk_map(b.z + (k < 2 ? k - 2 : k - 1), p.nz, p.bc_lo[2], p.bc_hi[2]);
+    }
     __syncthreads();
     // the first kBulkBufs items, item j by warp j % 8, in flight while the
     // moment sums load
     for_pops(std::make_integer_sequence<int, kBulkBufs>{}, [&](auto jc) {
         constexpr int j = decltype(jc)::value;
-        if (b.warp == j % 8) bulk_issue<19, j, LAT>(b, p, f, h, p.ps);
+        if (b.warp == j % 8) bulk_issue<19, j, LAT>(b, p, f, h);
     });
 
     const int x0 = b.x0t + 2 * tx, y = b.y0 + ty, z = b.z;
@@ -114,10 +120,6 @@ bool f32_bulk_eligible(const StepParams &p, int dim, int euler)
 
 cudaError_t make_tile_maps(const StepParams &p, const float *f, const float *h, TileMaps *out)
 {
-#ifdef RLB_BULK_ROWS_ONLY
-    (void)p; (void)f; (void)h; (void)out;
-    return cudaErrorNotSupported;
-#else
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         void *fn = nullptr;
@@ -143,7 +145,6 @@ cudaError_t make_tile_maps(const StepParams &p, const float *f, const float *h, 
         make(&out->hc, h, boxc) != CUDA_SUCCESS || make(&out->hz, h, boxz) != CUDA_SUCCESS)
         return cudaErrorInvalidValue;
     return cudaSuccess;
-#endif
 }
 
 cudaError_t launch_step_f32_bulk(const StepParams &p, const float *f, const float *h, float *fo, float *ho,
@@ -161,10 +162,9 @@ cudaError_t launch_step_f32_bulk(const StepParams &p, const float *f, const floa
         if (e != cudaSuccess) return e;
         if (dev < kMaxDevices) attr_set[dev].store(true, std::memory_order_release);
     }
+    if (!maps) return cudaErrorInvalidValue;
     const dim3 block(32, 8, 1), grid(unsigned(p.nx / 64), unsigned(p.ny / 8), unsigned(p.nz));
-    TileMaps none;
-    if (!maps) std::memset(&none, 0, sizeof(none));
-    f32::step_f32_bulk_kernel<0><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev, maps ? *maps : none, maps ? 1 : 0);
+    f32::step_f32_bulk_kernel<0><<<grid, block, smem, s>>>(p, f, h, fo, ho, prev, *maps);
     return cudaGetLastError();
 }
 
