@@ -156,7 +156,8 @@ RLB_API void rlb_default_options(rlb_options *opts);
 
 /* Validate a configuration on the host without touching the GPU.  Same
  * arguments and checks as rlb_create.  Rules: Q must be 19 (the extended
- * lattice of Sec. II.A, Eq. 42); nx, ny, nz >= 1 and N < 2^31; eta_over_s,
+ * lattice of Sec. II.A, Eq. 42); nx, ny, nz >= 1 and N < 2^31 (N < 2^30 in
+ * the FP32-storage form, which needs about 330 GB at 2^30); eta_over_s,
  * zeta_over_s >= 0; INLET only on x faces with n > 0, T > 0, |u| < 1;
  * RLB_E_UNSTABLE if dt/dx times the largest sum over moving axes of
  * |c_ia| c_0/c_t of the chosen lattice exceeds 1, or if 2 d (c_0 nu / c_t) dt alpha exceeds 1

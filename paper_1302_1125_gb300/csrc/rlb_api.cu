@@ -126,6 +126,9 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
         return fail(ctx, RLB_E_INVALID, "dt_over_dx must be finite and > 0");
     if (o.precision != RLB_FP64 && o.precision != RLB_FP32_STORAGE)
         return fail(ctx, RLB_E_INVALID, "unknown precision");
+    // the FP32 step addresses a population plane with 32-bit byte offsets
+    if (o.precision == RLB_FP32_STORAGE && (long long)g.nx * g.ny * g.nz >= (1LL << 30))
+        return fail(ctx, RLB_E_INVALID, "FP32-storage grids must have fewer than 2^30 cells");
     if (o.euler_mode != 0 && o.euler_mode != 1) return fail(ctx, RLB_E_INVALID, "euler_mode must be 0 or 1");
     if (o.symmetry_1d != 0 && o.symmetry_1d != 1) return fail(ctx, RLB_E_INVALID, "symmetry_1d must be 0 or 1");
     if (o.symmetry_1d) {

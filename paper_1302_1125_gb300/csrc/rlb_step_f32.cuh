@@ -63,6 +63,11 @@ struct Geo {
     int oa, oc;          // offsets of the pairs holding x0-2, x0-1 and x0+2, x0+3
     unsigned xfix;       // edge columns: clamp or ghost fix-ups (XF_*)
     int yoff[4], zoff[4];   // offsets of rows/planes at -2, -1, +1, +2 (mapped)
+    // 3-D staged step: byte offsets, from the start of a population plane, of
+    // the pairs a thread stages: x0-2, x0, x0+2 (mapped like oa, oc), then the
+    // rows at y-2, y-1, y+1, y+2 and the planes at z-2 .. z+2 (mapped); 32
+    // bits hold them since FP32 grids have fewer than 2^30 cells
+    unsigned sb[11];
 };
 // XF_HI_ODD1 / XF_HI_ODD3: odd-length tube stored with one pad cell, the pair
 // holds its last cell (x0 = nx - 1) or ends two cells before it (x0 = nx - 3)
@@ -516,8 +521,41 @@ __device__ __forceinline__ void stage_item(const float *f, const float *h, const
     constexpr int I = rep<NP>(IS_F ? J : J - NP);
     constexpr bool xneed = cdir<I, 0, LAT>() != 0 || (IS_F && I != 0);
     constexpr bool need_lap = IS_F && I != 0;
-    const float *q = (IS_F ? f : h) + I * ps + g.idx0;
     const unsigned d = dst0 + unsigned(J % kStageBufs) * stage_slots<DIM>() * sstride;
+    if constexpr (DIM == 3) {
+        // one population plane base for the block, the thread's fixed byte
+        // offsets on top (fewer address instructions than a per-thread base)
+        const char *qb = reinterpret_cast<const char *>((IS_F ? f : h) + I * ps);
+        auto at = [&](int s) { return reinterpret_cast<const float *>(qb + g.sb[s]); };
+        if constexpr (xneed) {
+            cp8(d + 0 * sstride, at(0));
+            cp8(d + 2 * sstride, at(2));
+        }
+        cp8(d + 1 * sstride, at(1));
+        auto axis = [&](auto ac) {
+            constexpr int A = decltype(ac)::value;
+            constexpr int c = cdir<I, A, LAT>();
+            constexpr int s0 = 3 + 4 * (A - 1);   // slots of distances -2, -1, +1, +2
+            const unsigned b = d + unsigned(3 * A) * sstride;
+            if constexpr (c > 0) {
+                cp8(b, at(s0 + 0));
+                cp8(b + sstride, at(s0 + 1));
+                cp8(b + 2 * sstride, at(s0 + 2));
+            } else if constexpr (c < 0) {
+                cp8(b, at(s0 + 1));
+                cp8(b + sstride, at(s0 + 2));
+                cp8(b + 2 * sstride, at(s0 + 3));
+            } else if constexpr (need_lap) {
+                cp8(b, at(s0 + 1));
+                cp8(b + sstride, at(s0 + 2));
+            }
+        };
+        axis(std::integral_constant<int, 1>{});
+        axis(std::integral_constant<int, 2>{});
+        cp_commit();
+        return;
+    }
+    const float *q = (IS_F ? f : h) + I * ps + g.idx0;
     if constexpr (xneed) {
         cp8(d + 0 * sstride, q + g.oa);
         cp8(d + 2 * sstride, q + g.oc);
@@ -890,6 +928,16 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
             bool gh;
             g.yoff[k] = DIM > 1 ? (map1(y + ds[k], p.ny, p.bc_lo[1], p.bc_hi[1], gh) - y) * p.nx : 0;
             g.zoff[k] = DIM > 2 ? (map1(z + ds[k], p.nz, p.bc_lo[2], p.bc_hi[2], gh) - z) * p.nx * p.ny : 0;
+        }
+    }
+    if constexpr (DIM == 3) {
+        g.sb[0] = 4u * unsigned(g.idx0 + g.oa);
+        g.sb[1] = 4u * unsigned(g.idx0);
+        g.sb[2] = 4u * unsigned(g.idx0 + g.oc);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            g.sb[3 + k] = 4u * unsigned(g.idx0 + g.yoff[k]);
+            g.sb[7 + k] = 4u * unsigned(g.idx0 + g.zoff[k]);
         }
     }
     // threads per block as the launcher sets them (rlb_step_f32_launch.cuh), a

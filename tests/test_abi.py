@@ -67,6 +67,10 @@ def cfg(**kw):
     ({"Q": 18}, rlb.RLB_E_INVALID),
     ({"nx": 0}, rlb.RLB_E_INVALID),
     ({"nx": 2048, "ny": 2048, "nz": 1024}, rlb.RLB_E_INVALID),
+    # the FP32 step addresses a population plane with 32-bit byte offsets
+    ({"nx": 1024, "ny": 1024, "nz": 1024, "precision": 1, "dt_over_dx": 0.15}, rlb.RLB_E_INVALID),
+    ({"nx": 1024, "ny": 1024, "nz": 1023, "precision": 1, "dt_over_dx": 0.15}, rlb.RLB_OK),
+    ({"nx": 1024, "ny": 1024, "nz": 1024, "precision": 0, "dt_over_dx": 0.15}, rlb.RLB_OK),
     ({"eta": -0.1}, rlb.RLB_E_INVALID),
     ({"zeta": math.nan}, rlb.RLB_E_INVALID),
     ({"limiter": 7}, rlb.RLB_E_INVALID),

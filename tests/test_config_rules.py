@@ -46,6 +46,7 @@ def expected(nx, ny, nz, lo, hi, inlet_n, inlet_T, inlet_u, eta, zeta, limiter, 
     invalid |= limiter not in (0, 1)
     invalid |= not (o["dt"] > 0 and math.isfinite(o["dt"]))
     invalid |= o["precision"] not in (0, 1) or o["euler"] not in (0, 1) or o["model"] not in (0, 1)
+    invalid |= o["precision"] == 1 and nx * ny * nz >= 2 ** 30
     invalid |= o["sym1"] not in (0, 1) or o["sym2"] not in (0, 1) or o["mapping"] not in (0, 1, 2, 3)
     if o["sym1"] == 1:
         invalid |= o["euler"] != 0 or ny != 1 or nz != 1 or (has_inlet and (inlet_u[1] != 0 or inlet_u[2] != 0))
