@@ -147,11 +147,21 @@ typedef struct {
                               * the float rate.  Supported with the extended lattice, the viscous step, even nx
                               * and no symmetry reduction; the threads always take tiles (1-D grids: the 1-D
                               * form).  rlb_create rejects other combinations with RLB_E_INVALID. */
+    int slab_rows;           /* RLB_FP32_STORAGE, 3-D grids, tiles: the order in which the blocks of
+                              * 64 x 8 cells start.  They take the grid in slabs of slab_rows block
+                              * rows (8 slab_rows cell rows), every z-plane of one slab before the
+                              * next slab, so that the z-neighbour planes the resident blocks read
+                              * stay in L2 for the blocks of the next planes.  0 (default): the
+                              * slab height whose one z-plane holds about 10 MB of f and h
+                              * (16 block rows at nx = 512); a value >= the grid's block rows:
+                              * the plain x, y, z order.  The results are the same bit for bit
+                              * whatever the order.  Must be >= 0; batched tubes: must be 0. */
 } rlb_options;
 
 /* Fill *opts with the defaults: dt/dx 0.25, no overrides, viscous mode, FP64,
  * default stream, no symmetry reduction, the extended lattice, automatic
- * thread mapping, double-float recovery (recovery_fp64 = 0). */
+ * thread mapping, double-float recovery (recovery_fp64 = 0), automatic slab
+ * height (slab_rows = 0). */
 RLB_API void rlb_default_options(rlb_options *opts);
 
 /* Validate a configuration on the host without touching the GPU.  Same

@@ -152,6 +152,7 @@ rlb_status validate(const rlb_grid *grid, int Q, double eta_over_s, double zeta_
             return fail(ctx, RLB_E_INVALID, "symmetry_2d needs inlet_u[2] = 0");
     }
     if (o.recovery_fp64 != 0 && o.recovery_fp64 != 1) return fail(ctx, RLB_E_INVALID, "recovery_fp64 must be 0 or 1");
+    if (o.slab_rows < 0) return fail(ctx, RLB_E_INVALID, "slab_rows must be >= 0");
     if (o.recovery_fp64) {
         if (o.precision != RLB_FP32_STORAGE)
             return fail(ctx, RLB_E_INVALID, "recovery_fp64 is an option of the FP32-storage form");
@@ -258,6 +259,7 @@ void rlb_default_options(rlb_options *o)
     o->thread_mapping = 0;
     o->symmetry_2d = 0;
     o->recovery_fp64 = 0;
+    o->slab_rows = 0;
 }
 
 rlb_status rlb_check_config(const rlb_grid *grid, int Q, double eta_over_s, double zeta_over_s,
@@ -353,6 +355,7 @@ rlb_status rlb_create(const rlb_grid *grid, int Q, double eta_over_s, double zet
     sp.half_lim = limiter == RLB_LIMITER_MINMOD ? 0.5 : 0.0;
     sp.lat = o.model;
     sp.mapping = o.thread_mapping;
+    sp.slab_by = o.slab_rows > 0 ? o.slab_rows : rlb::f32_slab_rows(grid->nx, grid->ny);
     sp.sym = o.symmetry_1d ? 1 : (o.symmetry_2d ? 2 : 0);
     sp.k1 = lat_c0ct(o.model) * o.dt_over_dx;
     sp.k2 = double(lat_dmag(o.model)) * lat_c0ct(o.model) * o.dt_over_dx;

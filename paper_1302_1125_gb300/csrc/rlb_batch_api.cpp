@@ -380,6 +380,7 @@ rlb_status rlb_batch_create(int B, const int *nx, const double *eta_over_s, cons
     if (o.model != 0) return bfail(nullptr, RLB_E_INVALID, "the batched path runs the extended lattice (model 0)");
     if (o.recovery_fp64 != 0)
         return bfail(nullptr, RLB_E_INVALID, "the batched path runs the double-float recovery (recovery_fp64 = 0)");
+    if (o.slab_rows != 0) return bfail(nullptr, RLB_E_INVALID, "slab_rows is an option of grids (0 for batches)");
     if (limiter != RLB_LIMITER_MINMOD && limiter != RLB_LIMITER_NONE)
         return bfail(nullptr, RLB_E_INVALID, "unknown limiter");
     if (!(o.dt_over_dx > 0.0) || !std::isfinite(o.dt_over_dx))

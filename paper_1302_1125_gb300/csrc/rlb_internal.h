@@ -25,6 +25,8 @@ struct StepParams {
                              // copies where eligible (rlb_options.thread_mapping)
     int sym;                 // grids: exact symmetry reduction, 1 on 1-D grids (7 planes per
                              // distribution), 2 on 2-D grids (14 planes: mirror images in z), 0 none
+    int slab_by;             // FP32 3-D tiles: blocks are taken in slabs of this many block rows,
+                             // z-planes in order within a slab (>= the block rows: x, y, z order)
     // float copies for the FP32-storage kernel (no FP64 conversion on device)
     float f_k1, f_k2, f_half_lim, f_kw, f_kbulk, f_eta_over_s, f_tau_override;
     float f_ghost_f[19], f_ghost_h[19];
@@ -52,6 +54,8 @@ bool f32_bulk_eligible(const StepParams &p, int dim, int euler);
 cudaError_t make_tile_maps(const StepParams &p, const float *f, const float *h, TileMaps *out);
 cudaError_t launch_step_f32_bulk(const StepParams &p, const float *f, const float *h, float *fo, float *ho,
                                  float *prev, const TileMaps *maps, cudaStream_t s);
+// block rows per slab of the FP32 3-D tiled step (StepParams::slab_by)
+int f32_slab_rows(int nx, int ny);
 // name of the step kernel launch_step_f64 / launch_step_f32 picks for p (see rlb_step_kernel)
 const char *f64_step_kernel_name(const StepParams &p, int dim);
 const char *f32_step_kernel_name(const StepParams &p, int dim, int euler, bool have_maps);

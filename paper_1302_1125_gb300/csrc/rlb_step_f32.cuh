@@ -858,6 +858,7 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
 #ifndef RLB_F32_BY
 #define RLB_F32_BY 8
 #endif
+
 constexpr int kParkSlots = 11;   // f2 slots per thread in shared memory
 #ifdef RLB_NO_PARK
 constexpr bool kParkOn = false;
@@ -896,9 +897,28 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
         z = int(row / unsigned(p.ny));
         if (z >= p.nz) return;
     } else {
-        x0 = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-        y = blockIdx.y * blockDim.y + threadIdx.y;
-        z = blockIdx.z;
+        unsigned bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+        if constexpr (DIM == 3) {
+            // blocks taken in slabs of p.slab_by block rows, z-planes in
+            // order within a slab (blocks start in the order of their linear
+            // index): the planes the z-stencils of the resident blocks read
+            // stay in L2 until the blocks of the neighbouring planes have
+            // read them, instead of a whole z-plane of the grid per step in z
+            const unsigned nbx = gridDim.x, nby = gridDim.y, nbz = gridDim.z, sb = unsigned(p.slab_by);
+            if (sb > 0u && sb < nby) {
+                const unsigned L = blockIdx.x + nbx * (blockIdx.y + nby * blockIdx.z);
+                const unsigned s = L / (nbx * sb * nbz);
+                const unsigned rows = min(sb, nby - s * sb);
+                const unsigned r = L - s * (nbx * sb * nbz);
+                bz = r / (nbx * rows);
+                const unsigned q = r - bz * (nbx * rows);
+                by = s * sb + q / nbx;
+                bx = q - (q / nbx) * nbx;
+            }
+        }
+        x0 = 2 * (bx * blockDim.x + threadIdx.x);
+        y = by * blockDim.y + threadIdx.y;
+        z = bz;
         if (x0 >= p.nx || y >= p.ny) return;
     }
     const long long ps = p.ps;

@@ -39,7 +39,7 @@ class rlb_options(C.Structure):
                 ("alpha_override", C.c_double), ("euler_mode", C.c_int),
                 ("precision", C.c_int), ("cuda_stream", C.c_void_p), ("symmetry_1d", C.c_int),
                 ("model", C.c_int), ("thread_mapping", C.c_int), ("symmetry_2d", C.c_int),
-                ("recovery_fp64", C.c_int)]
+                ("recovery_fp64", C.c_int), ("slab_rows", C.c_int)]
 
 
 class rlb_batch_tuning(C.Structure):
@@ -166,10 +166,10 @@ def make_grid(nx, ny=1, nz=1, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
 
 def make_options(dt_over_dx=0.25, tau_override=0.0, alpha_override=-1.0, euler_mode=0,
                  precision=FP64, cuda_stream=None, symmetry_1d=0, model=MODEL_EXTENDED,
-                 thread_mapping=MAPPING_AUTO, symmetry_2d=0, recovery_fp64=0):
+                 thread_mapping=MAPPING_AUTO, symmetry_2d=0, recovery_fp64=0, slab_rows=0):
     return rlb_options(float(dt_over_dx), float(tau_override), float(alpha_override),
                        int(euler_mode), int(precision), cuda_stream, int(symmetry_1d), int(model),
-                       int(thread_mapping), int(symmetry_2d), int(recovery_fp64))
+                       int(thread_mapping), int(symmetry_2d), int(recovery_fp64), int(slab_rows))
 
 
 def rlb_check_config(grid, Q, eta_over_s, zeta_over_s, limiter, opts) -> int:
@@ -303,14 +303,15 @@ class Grid:
     MAPPING_LINEAR; the results are the same) and the exact symmetry
     reductions (symmetry_1d on grids with ny = nz = 1, symmetry_2d on grids
     with nz = 1; viscous step), and for FP32_STORAGE the FP64 Landau-frame
-    recovery (recovery_fp64 = 1)."""
+    recovery (recovery_fp64 = 1) and the block order of the 3-D tiles
+    (slab_rows; 0 automatic; the results are the same)."""
 
     def __init__(self, nx, ny=1, nz=1, *, bc_lo=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC),
                  bc_hi=(BC_OUTFLOW, BC_PERIODIC, BC_PERIODIC), inlet=(1.0, 1.0, (0.0, 0.0, 0.0)),
                  eta_over_s=0.1, zeta_over_s=0.0, limiter=LIMITER_MINMOD, dt_over_dx=0.25,
                  tau_override=0.0, alpha_override=-1.0, euler_mode=0, precision=FP64,
                  model=MODEL_EXTENDED, stream="current", thread_mapping=0, symmetry_1d=0, symmetry_2d=0,
-                 recovery_fp64=0):
+                 recovery_fp64=0, slab_rows=0):
         self.nx, self.ny, self.nz = int(nx), int(ny), int(nz)
         self.N = self.nx * self.ny * self.nz
         self.precision = int(precision)
@@ -318,7 +319,8 @@ class Grid:
         self._grid = make_grid(nx, ny, nz, bc_lo, bc_hi, inlet)
         self._opts = make_options(dt_over_dx, tau_override, alpha_override, euler_mode, precision, s,
                                   symmetry_1d=symmetry_1d, model=model, thread_mapping=thread_mapping,
-                                  symmetry_2d=symmetry_2d, recovery_fp64=recovery_fp64)
+                                  symmetry_2d=symmetry_2d, recovery_fp64=recovery_fp64,
+                                  slab_rows=slab_rows)
         self.ctx = rlb_create(self._grid, Q, eta_over_s, zeta_over_s, limiter, self._opts)
 
     @classmethod

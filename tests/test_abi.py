@@ -57,7 +57,7 @@ def cfg(**kw):
         if k in g:
             g[k] = kw.pop(k)
         elif k in ("dt_over_dx", "tau_override", "alpha_override", "euler_mode", "precision", "symmetry_1d",
-                   "model", "thread_mapping", "symmetry_2d"):
+                   "model", "thread_mapping", "symmetry_2d", "slab_rows"):
             o[k] = kw.pop(k)
     return rlb.make_grid(**g), rlb.make_options(**o), kw
 
@@ -93,6 +93,8 @@ def cfg(**kw):
       "inlet": (1.0, 1.0, (0.5, 0.1, 0.0))}, rlb.RLB_E_INVALID),          # inlet moving in y
     ({"model": 2}, rlb.RLB_E_INVALID),
     ({"thread_mapping": 4}, rlb.RLB_E_INVALID),
+    ({"slab_rows": -1}, rlb.RLB_E_INVALID),
+    ({"slab_rows": 3, "ny": 64, "nz": 8, "precision": 1, "dt_over_dx": 0.15}, rlb.RLB_OK),
     ({"thread_mapping": 3, "ny": 8, "nz": 8}, rlb.RLB_OK),
     ({"thread_mapping": -1}, rlb.RLB_E_INVALID),
     ({"thread_mapping": 2, "ny": 8, "nz": 8}, rlb.RLB_OK),
