@@ -852,6 +852,26 @@ __device__ __forceinline__ void update_pair(const StepParams &p, const Geo &g, f
     }
 }
 
+// The tile (bx, by, bz) of this block when blocks are taken in slabs of
+// slab_by block rows, z-planes in order within a slab (blocks start in the
+// order of their linear index): the planes the z-stencils of the resident
+// blocks read stay in L2 until the blocks of the neighbouring planes have
+// read them, instead of a whole z-plane of the grid per step in z.
+// slab_by = 0 or >= the block rows: the plain x, y, z order.
+__device__ __forceinline__ void slab_order(int slab_by, unsigned &bx, unsigned &by, unsigned &bz)
+{
+    const unsigned nbx = gridDim.x, nby = gridDim.y, nbz = gridDim.z, sb = unsigned(slab_by);
+    if (sb == 0u || sb >= nby) return;
+    const unsigned L = blockIdx.x + nbx * (blockIdx.y + nby * blockIdx.z);
+    const unsigned s = L / (nbx * sb * nbz);
+    const unsigned rows = min(sb, nby - s * sb);
+    const unsigned r = L - s * (nbx * sb * nbz);
+    bz = r / (nbx * rows);
+    const unsigned q = r - bz * (nbx * rows);
+    by = s * sb + q / nbx;
+    bx = q - (q / nbx) * nbx;
+}
+
 #ifndef RLB_F32_MINB
 #define RLB_F32_MINB 2
 #endif
@@ -898,24 +918,7 @@ __global__ void __launch_bounds__(32 * RLB_F32_BY, VEC2 ? RLB_F32_MINB : 1)
         if (z >= p.nz) return;
     } else {
         unsigned bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
-        if constexpr (DIM == 3) {
-            // blocks taken in slabs of p.slab_by block rows, z-planes in
-            // order within a slab (blocks start in the order of their linear
-            // index): the planes the z-stencils of the resident blocks read
-            // stay in L2 until the blocks of the neighbouring planes have
-            // read them, instead of a whole z-plane of the grid per step in z
-            const unsigned nbx = gridDim.x, nby = gridDim.y, nbz = gridDim.z, sb = unsigned(p.slab_by);
-            if (sb > 0u && sb < nby) {
-                const unsigned L = blockIdx.x + nbx * (blockIdx.y + nby * blockIdx.z);
-                const unsigned s = L / (nbx * sb * nbz);
-                const unsigned rows = min(sb, nby - s * sb);
-                const unsigned r = L - s * (nbx * sb * nbz);
-                bz = r / (nbx * rows);
-                const unsigned q = r - bz * (nbx * rows);
-                by = s * sb + q / nbx;
-                bx = q - (q / nbx) * nbx;
-            }
-        }
+        if constexpr (DIM == 3) slab_order(p.slab_by, bx, by, bz);
         x0 = 2 * (bx * blockDim.x + threadIdx.x);
         y = by * blockDim.y + threadIdx.y;
         z = bz;

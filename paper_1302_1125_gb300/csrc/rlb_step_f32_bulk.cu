@@ -47,9 +47,11 @@ __global__ void __launch_bounds__(kBulkThreads, 2)
     b.issued = issued;
     b.warp = ty;
     b.lane = tx;
-    b.x0t = 64 * int(blockIdx.x);
-    b.y0 = 8 * int(blockIdx.y);
-    b.z = int(blockIdx.z);
+    unsigned bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    slab_order(p.slab_by, bx, by, bz);   // the per-thread staged kernel's block order
+    b.x0t = 64 * int(bx);
+    b.y0 = 8 * int(by);
+    b.z = int(bz);
     b.cxlo = b.x0t == 0 ? 0 : b.x0t - 4;
     b.cxhi = b.x0t + 64 == p.nx ? p.nx : b.x0t + 68;
     b.ymap = ymap;

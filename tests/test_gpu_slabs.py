@@ -6,8 +6,9 @@ Each block computes the same 64 x 8 cells whatever its place in the order,
 and a step reads only the previous buffers, so every slab height gives the
 state of the plain x, y, z order bit for bit: full slabs, a ragged last slab
 (block rows not a multiple of the slab height), one-row slabs, the automatic
-height on a grid wide enough to use it, and the FP64-recovery variant of the
-kernel.  The oracle parity of the step is tests/test_gpu_parity.py's.
+height on a grid wide enough to use it, the FP64-recovery variant of the
+kernel and the bulk-staged kernel (thread_mapping 3), which takes the same
+order.  The oracle parity of the step is tests/test_gpu_parity.py's.
 """
 import numpy as np
 import pytest
@@ -78,4 +79,20 @@ def test_slab_order_of_the_fp64_recovery_variant():
     k1, slab = _state(w, 2, 10, recovery_fp64=1)
     assert k0 == k1 == "fp32_rec64"
     for a, b in zip(plain, slab):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("slab_rows", [1, 4])
+def test_slab_order_of_the_bulk_staged_kernel(slab_rows):
+    # thread_mapping 3: the block-wide bulk-copy kernel takes the same order
+    w = _box(192, 48, 7, seed=24, lo=(2, 1, 1), hi=(1, 1, 1))
+    _, plain = _state(w, 1000, 12)
+    g = rlb.Grid.from_workload(w, precision=rlb.FP32_STORAGE, thread_mapping=rlb.MAPPING_BULK_TILES,
+                               slab_rows=slab_rows)
+    g.init(*[torch.as_tensor(a, device="cuda") for a in w.fields()])
+    assert g.step_kernel == "fp32_bulk_tiles"
+    g.step(12)
+    bulk = g.get_state()
+    g.close()
+    for a, b in zip(plain, bulk):
         assert np.array_equal(a, b)
