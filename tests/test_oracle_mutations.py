@@ -17,8 +17,9 @@ Eq. 57 applied to the number distribution as well; an inlet ghost whose
 pressure drops the temperature; open ends that reflect instead of copying
 the edge cell; the h equation relaxing to h^eq(t) instead of the
 extrapolated 2 h^eq(t) - h^eq(t - dt), and the f equation doing the same;
-nu = 1 in place of sqrt(13) in every constant of the extended lattice (the
-survey's reading, which the tests of the readings reject).
+nu = 1 in place of sqrt(13) in every constant of the extended lattice (a
+reading of the garbled lattice constants that the tests of the readings
+reject).
 """
 import os
 import subprocess
