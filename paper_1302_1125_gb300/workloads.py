@@ -112,7 +112,7 @@ def _tube_fields(nx, ny, nz, left, right, x0=None):
     sel = (x < x0)
     def col(a, b):
         v = np.where(sel, a, b).astype(np.float64)
-        return np.ascontiguousarray(np.broadcast_to(v, (nz, ny, nx)).reshape(-1))
+        return np.array(np.broadcast_to(v, (nz, ny, nx)).reshape(-1))   # a writable copy
     n = col(left[0], right[0])
     T = col(left[1], right[1])
     ux = col(left[2], right[2])
@@ -297,7 +297,7 @@ def boosted_box(nx, ny=1, nz=1, *, gamma=10.0, direction=(1.0, 0.0, 0.0), amp=1e
     n1 = float(n_eq(1.0)) * (1.0 + 0.5 * amp * np.cos(2 * math.pi * x / nx + 2.0))
 
     def col(v):
-        return np.ascontiguousarray(np.broadcast_to(v, (nz, ny, nx)).reshape(-1), np.float64)
+        return np.array(np.broadcast_to(v, (nz, ny, nx)).reshape(-1), np.float64)   # a writable copy
     fl = [col(n1), col(T1)] + [col(np.full(nx, beta * d[a])) for a in range(3)]
     per = (BC_PERIODIC, BC_PERIODIC, BC_PERIODIC)
     return Workload(name, nx, ny, nz, per, per, dt_over_dx, 0.05, 0.0, steps, precision,
